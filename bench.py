@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 IB-GM time step (Wiens & Stockie, arxiv 1305.3976).
+
+Workload (one "step" = one full IB-GM time step, Sec. 3.4 Steps 1a-3f): 3D
+ellipsoidal membrane in the periodic unit cube, 128^3 MAC grid, rho = 1,
+mu = 0.05, semi-axes 0.2/0.25/0.3, icosahedral nu = 64 mesh (40962 markers,
+122880 force connections, sigma = 1), dt = 5e-4; FP32 fields, FP64 markers.
+Synthetic, seeded inputs.  L2 is flushed (a 256 MiB write) before every timed
+step; each step is timed with CUDA events on the stream that launches it.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the same workload instead (rank 0 only; other ranks exit without work).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IB steps/s & cell-updates/s FP32 vs FP64 on one GB300; line-solve HBM GB/s"
+WORKLOAD = ("3D ellipsoidal membrane, 128^3 periodic MAC grid, rho=1, mu=0.05, semi-axes 0.2/0.25/0.3, "
+            "icosahedral nu=64 mesh (40962 markers, 122880 springs, sigma=1), dt=5e-4, FP32 fields, FP64 markers")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--nu", type=int, default=64)
+    ap.add_argument("--quick", action="store_true", help="skip the FP64, line-solve, e2e and CPU legs")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def scene(args):
+    from paper_1305_3976_gb300 import inputs as I
+    return I.ellipsoid_3d(n=args.n, nu=args.nu)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel slot (3D, w bytes per field word)
+
+
+def kernel_bytes(name, cells, nm, ne, w, d=3):
+    m = {
+        # marker arrays (FP64) + one field word per node of the 4^d stencil
+        "interp": nm * (4 * d * 8 + 4 ** d * d * w),
+        # own Xh, X, U, Uold (rw), G; neighbour Xh, CSR col/kappa/rest
+        "force": nm * (d * 8 * 7 + 8) + 2 * ne * (d * 8 + 4 + 16),
+        # Xh, G per marker + one read-modify-write field word per node
+        "spread": nm * (2 * d * 8 + 4 ** d * d * 2 * w),
+        # u(3), p, psi, f(3), N(u^{n-1})(3) in; R(3), N(u^n)(3) out
+        "rhs": cells * w * (4 * d + 5),
+        "mom_sweep_1": cells * w * 2 * d,
+        "mom_sweep_2": cells * w * 2 * d,
+        "mom_sweep_3": cells * w * 4 * d,   # e in, u^n in/out, scratch cleared
+        "psi_sweep_1": cells * w * (d + 5), # u(3), div, p in; psi, div, p out
+        "psi_sweep_2": cells * w * 2,
+        "psi_sweep_3": cells * w * 4,       # psi, p in; psi, p out
+    }
+    return m[name]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1305_3976_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        t = json.load(open(p))
+    except Exception:
+        return None
+    if t.get("source_hash") != source_hash():
+        return None
+    return t.get("kernels", {}).get(kernel)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle as O
+    sc = scene(args)
+    P = O.params(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
+    sim = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
+    steps = max(1, min(args.steps, 2))   # each oracle step takes ~10 s on one core
+    warm = min(args.warmup, 0)
+    sim.step(warm)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    cells = sc.cells
+    val = cells * steps / dt
+    sample = f"{steps} oracle step(s) of the {args.n}^3 workload (requested --steps {args.steps})"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("FP32 fields", "FP64 fields (oracle)"), "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1305_3976_gb300 as ib
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    sc = scene(args)
+    cells, nm, ne = sc.cells, sc.X.shape[0], sc.edges.shape[0]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 129 MB L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make_grid(prec):
+        g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=prec, kernel=sc.kernel,
+                    rotate_split=True)
+        g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+        return g
+
+    def timed_steps(g, K, W):
+        g.step(W)
+        barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for i in range(K):
+            flush.zero_()
+            starts[i].record()
+            g.step(1)
+            ends[i].record()
+        barrier()
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends))   # ms
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prec = args.precision
+    w = 4 if prec == "fp32" else 8
+    g = make_grid(prec)
+    clocks = Clocks(local)
+    clocks.start()
+    tot_ms = timed_steps(g, args.steps, args.warmup)
+    clk = clocks.stop()
+    tot_ms = max_over_ranks(tot_ms)
+    ms_step = tot_ms / args.steps
+    value = cells * args.steps * world / (tot_ms * 1e-3)
+
+    # per-kernel durations: every kernel launched on its own, CUDA events on
+    # the launching stream, L2 flushed before each step
+    prof = {}
+    nprof = 6
+    for _ in range(nprof):
+        flush.zero_()
+        torch.cuda.synchronize()
+        for k, v in g.profile(1).items():
+            prof[k] = prof.get(k, 0.0) + v
+    per_launch = {k: v / nprof for k, v in prof.items()}
+    dom = max(per_launch, key=per_launch.get)
+    hbm, peak_kind = peaks()
+    ab = kernel_bytes(dom, cells, nm, ne, w)
+    achieved = ab / (per_launch[dom] * 1e-3) / 1e9
+    diag = g.diagnostics()
+    g.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32 fields", "FP64 fields"),
+                   "cells": cells, "markers": nm, "springs": ne,
+                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "steps_per_s": 1e3 / ms_step * world,
+        "kernels_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom)},
+        "gpu_launches": args.steps * (10 if nm else 7),
+        "clocks": clk,
+        "state_check": {"volume": diag["volume"], "div_l2": diag["div_l2"], "kinetic": diag["kinetic"]},
+    }
+
+    if not args.quick:
+        # FP64 fields on the same workload
+        if prec == "fp32":
+            g64 = make_grid("fp64")
+            k64 = max(5, args.steps // 2)
+            ms64 = max_over_ranks(timed_steps(g64, k64, args.warmup)) / k64
+            g64.close()
+            out["fp64"] = {"value": cells * world / (ms64 * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms64,
+                           "steps_per_s": 1e3 / ms64 * world, "steps": k64}
+        # line-solve microbench: the paper's Poisson-comparison operator at 512^3
+        N = 512
+        f = torch.randn(N, N, N, dtype=torch.float32, device=dev)
+        psi = torch.empty_like(f)
+        r = (float(N * N),) * 3
+        for _ in range(3):
+            ib.ib_split_solve(ib.IB_FP32, 3, (N, N, N), r, f, psi)
+        torch.cuda.synchronize()
+        reps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ib.ib_split_solve(ib.IB_FP32, 3, (N, N, N), r, f, psi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_ls = e0.elapsed_time(e1) / reps
+        ls_bytes = 3 * 2 * 4 * N ** 3
+        out["line_solve"] = {"workload": "(1-D_xx)(1-D_yy)(1-D_zz) psi = f, 512^3 FP32, r = N^2, 3 sweeps",
+                             "ms": ms_ls, "GB_per_s": ls_bytes / (ms_ls * 1e-3) / 1e9,
+                             "frac": ls_bytes / (ms_ls * 1e-3) / 1e9 / hbm,
+                             "cell_updates_per_s": N ** 3 / (ms_ls * 1e-3)}
+        del f, psi
+        # end to end through the C ABI with host buffers: every step the marker
+        # positions come from pinned host memory and go back to it
+        ge = make_grid(prec)
+        ge.step(args.warmup)
+        Xh = torch.empty((nm, 3), dtype=torch.float64, pin_memory=True).numpy()
+        ib.ib_read_markers(ge.h, Xh)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ib.ib_set_markers(ge.h, Xh)
+            ib.ib_step(ge.h, 1)
+            ib.ib_read_markers(ge.h, Xh)
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        ge.close()
+        out["e2e"] = {"value": cells * args.steps * world / te, "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": nm * 3 * 8, "d2h_bytes_per_step": nm * 3 * 8,
+                      "what": "per step: ib_set_markers from pinned host memory, ib_step, ib_read_markers to host"}
+        # the oracle on this host's cores, one step of the same workload
+        if rank == 0 and world == 1:
+            import oracle as O
+            P = O.params(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
+            sim = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
+            t0 = time.perf_counter()
+            sim.step(1)
+            tc = time.perf_counter() - t0
+            out["cpu_baseline"] = {"value": cells / tc, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"1 step of the {args.n}^3 workload ({tc:.1f} s, FP64, one thread)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * ib_gb300.h -- C ABI of the GB300 (sm_103a) implementation of one IB-GM time
+ * step of Wiens & Stockie, "An Efficient Parallel Immersed Boundary Algorithm
+ * using a Pseudo-Compressible Fluid Solver" (arxiv 1305.3976), Sec. 3.4.
+ *
+ * Conventions shared by every entry point
+ *   - Return IB_OK (0) or a negative IB_ERR_* code; ib_last_error() gives a
+ *     message for the calling thread's most recent failure.  No entry point
+ *     aborts, traps or prints.
+ *   - Plain pointers only.  A pointer argument is host memory unless its
+ *     `*_on_device` flag (or the entry point) says it is a CUDA device
+ *     pointer of the current device.
+ *   - Inputs are copied: the caller keeps ownership of every buffer it passes
+ *     and may free it when the call returns.  The library owns the device
+ *     state behind an ib_grid_t and frees it in ib_destroy_grid.
+ *   - Work is stream-ordered on the stream given in ib_grid_desc.stream (a
+ *     cudaStream_t; NULL means the legacy default stream).  Calls that return
+ *     data to host memory synchronise that stream before returning.
+ *   - Fields are stored SoA, x fastest: index i + n0 (j + n1 k).  Velocity
+ *     component c lives on the c-faces of the MAC grid (Sec. 3.2, Fig. 1):
+ *     u at (i h, (j+1/2) h, (k+1/2) h), v at ((i+1/2) h, j h, (k+1/2) h),
+ *     w at ((i+1/2) h, (j+1/2) h, k h); p and psi at cell centres.
+ *   - Markers are FP64, array-of-structs [n_markers][dim], unwrapped (the
+ *     periodic wrap is applied to grid indices only).
+ */
+#ifndef IB_GB300_H
+#define IB_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  IB_OK = 0,
+  IB_ERR_ARG = -1,       /* invalid argument (null pointer, size, range)       */
+  IB_ERR_OOM = -2,       /* device or host allocation failed                    */
+  IB_ERR_CUDA = -3,      /* a CUDA runtime call failed (see ib_last_error)      */
+  IB_ERR_NONFINITE = -4, /* a NaN or Inf was found in the state                 */
+  IB_ERR_TIMEOUT = -5,   /* reserved: a bounded device-side wait ran out        */
+  IB_ERR_STATE = -6      /* call not allowed in the grid's current state        */
+};
+
+enum { IB_FP32 = 0, IB_FP64 = 1 };                 /* field precision          */
+enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };  /* 1D kernel phi(r)         */
+
+/* field selection bits for ib_read_fields */
+enum {
+  IB_FIELD_U = 1, IB_FIELD_V = 2, IB_FIELD_W = 4,
+  IB_FIELD_P = 8,    /* p^{n-1/2} after n steps                       */
+  IB_FIELD_PSI = 16, /* psi^{n-1/2}                                   */
+  IB_FIELD_DIV = 32  /* D.u^n (cell centres)                          */
+};
+
+typedef struct ib_grid_s *ib_grid_t;
+
+/* Problem description (Sec. 3.2-3.4).
+ *   dim          2 or 3.
+ *   n[3]         cells per axis, each 8 <= n <= 512 (n[2] ignored in 2D);
+ *                h_a = H / n[a].
+ *   H            side of the periodic box [0,H]^d.
+ *   rho, mu      density and dynamic viscosity (eq. NSE).
+ *   dt           time step (also the perturbation parameter epsilon).
+ *   chi          weight of the pressure update, Step 3f (the paper uses 0.6).
+ *   precision    IB_FP32 or IB_FP64 fields; markers are always FP64.
+ *   kernel       IB_DELTA_PESKIN4 (eq. discretedelta) or IB_DELTA_COS4
+ *                (phi = (1 + cos(pi r / 2)) / 4 on |r| < 2).
+ *   rotate_split 1: step n applies the direction-split factors in the order
+ *                cyclically shifted by n mod dim (Sec. 4.1); 0: x, y(, z).
+ *   stream       cudaStream_t the grid works on (NULL: default stream).      */
+typedef struct {
+  int dim;
+  int n[3];
+  double H, rho, mu, dt, chi;
+  int precision;
+  int kernel;
+  int rotate_split;
+  void *stream;
+} ib_grid_desc;
+
+/* FP64 diagnostics (Sec. 5.1 volume conservation; discrete l2 norms of
+ * eqs. ScalarDiscreteL2 / VectorDiscreteL2). */
+typedef struct {
+  double volume;   /* area (2D, from the oriented edge loops) or volume (3D,
+                      from the oriented triangles passed to ib_add_fiber)      */
+  double div_l2;   /* (h^d sum (D.u)^2)^{1/2}                                 */
+  double div_max;  /* max |D.u|                                               */
+  double kinetic;  /* 1/2 rho h^d sum |u|^2                                   */
+  double elastic;  /* sum over connections 1/2 kappa (|X_b - X_a| - L)^2 at X^n */
+  int64_t step;    /* n                                                      */
+} ib_diag;
+
+/* Create a grid with u = 0, p = psi = 0 and no markers (Sec. 3.4, n = 0).
+ * Allocates (3 dim + 3) fields of n0 n1 n2 elements on the current device.
+ * Errors: IB_ERR_ARG (bad desc), IB_ERR_OOM, IB_ERR_CUDA. */
+int ib_create_grid(const ib_grid_desc *desc, ib_grid_t *out);
+
+/* Append one structure made of points and force connections (Sec. 4.1,
+ * Fig. 3; Step 2a): connection e joins points edges[2e], edges[2e+1] (indices
+ * local to this call, 0 <= index < n_markers) and pulls them together with
+ *   T_e = kappa[e] (X_b - X_a) (1 - rest_len[e] / |X_b - X_a|),
+ * the difference taken through the nearest periodic image.  A closed 2D fiber
+ * of N_s points with kappa = sigma / h_s and rest_len = L h_s reproduces the
+ * paper's F_k h_s.  rest_len may be NULL (all zero).  tris (optional, 3D:
+ * [n_tris][3] outward-oriented triangles; 2D: ignored, the directed edges give
+ * the area) feed ib_diagnostics.  All arrays are host memory.  Only allowed
+ * before the first step.  fiber_id_out (optional) receives the structure's
+ * index.  Errors: IB_ERR_ARG, IB_ERR_STATE, IB_ERR_OOM, IB_ERR_CUDA. */
+int ib_add_fiber(ib_grid_t g, const double *X0, int64_t n_markers, const int32_t *edges,
+                 const double *kappa, const double *rest_len, int64_t n_edges,
+                 const int32_t *tris, int64_t n_tris, int32_t *fiber_id_out);
+
+/* Set velocity component comp (0..dim-1) from n0 n1 n2 elements of the
+ * grid's precision (host memory, or device memory if on_device).  Only
+ * allowed before the first step.  Errors: IB_ERR_ARG, IB_ERR_STATE, IB_ERR_CUDA. */
+int ib_set_velocity(ib_grid_t g, int comp, const void *src, int on_device);
+
+/* Advance n_steps IB-GM steps (Sec. 3.4, Steps 1a-3f; the first step uses the
+ * n = 0 replacements).  Asynchronous on the grid's stream.
+ * Errors: IB_ERR_ARG (n_steps < 0), IB_ERR_CUDA. */
+int ib_step(ib_grid_t g, int n_steps);
+
+/* Copy the fields selected by field_mask, in the bit order U, V, W, P, PSI,
+ * DIV, each n0 n1 n2 elements of the grid's precision, back to back into dst
+ * (bytes must equal the total).  Host dst: the call returns when the data is
+ * there; device dst: stream-ordered.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_read_fields(ib_grid_t g, unsigned field_mask, void *dst, size_t bytes, int dst_on_device);
+
+/* Copy the marker positions X^n ([n][dim] FP64, all structures in the order
+ * they were added) to X; n must equal the total marker count.
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_read_markers(ib_grid_t g, double *X, int64_t n, int dst_on_device);
+
+/* Replace the marker positions X^n (for example by a host-side structure
+ * model coupled to the fluid); U^{n-1} is kept.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_set_markers(ib_grid_t g, const double *X, int64_t n, int src_on_device);
+
+/* FP64 diagnostics of the current state; synchronises the grid's stream.
+ * Returns IB_ERR_NONFINITE (after filling *out) if any value is NaN or Inf. */
+int ib_diagnostics(ib_grid_t g, ib_diag *out);
+
+/* Release every device and host resource of the grid. */
+int ib_destroy_grid(ib_grid_t g);
+
+/* Static text for an IB_* code; message of the calling thread's last error. */
+const char *ib_error_string(int code);
+const char *ib_last_error(void);
+
+/* Batched constant-coefficient cyclic tridiagonal solve along one axis
+ * (Sec. 4.2, eq. TriDiagX): every line along `axis` of the n0 x n1 x n2 field
+ * `in` is replaced by the solution x of
+ *   (1 + 2r) x_i - r x_{i-1} - r x_{i+1} = b_i   (indices mod n[axis]),
+ * written to `out` (device pointers of the given precision; out may equal in).
+ * dim 2 ignores n[2]; 8 <= n[a] <= 512.  r >= 0.  Stream-ordered on `stream`.
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_cyclic_solve_lines(int precision, int dim, const int n[3], int axis, double r,
+                          const void *in, void *out, void *stream);
+
+/* The direction-split operator of the paper's Poisson comparison (Sec. 6.1,
+ * eq. PoissonGMProblem) and of Step 3e: solves
+ *   (I - r_0 D2_x)(I - r_1 D2_y)[(I - r_2 D2_z)] psi = f
+ * with D2 the unit periodic second difference (for Step 3e, r_a = 1/h_a^2)
+ * as one sweep per axis: f (device) -> psi (device; may equal f).
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_split_solve(int precision, int dim, const int n[3], const double r[3], const void *f,
+                   void *psi, void *stream);
+
+/* Run n_steps steps with every kernel launched on its own and timed by CUDA
+ * events on the grid's stream; kernel_ms[i] receives the total milliseconds
+ * of kernel slot i (at most max_kernels slots, *n_kernels gets the count) and
+ * ib_kernel_name(i) its name.  Advances the state like ib_step.
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels, int *n_kernels);
+const char *ib_kernel_name(int slot);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IB_GB300_H */

@@ -1,1 +1,289 @@
-"""GB300-native IB-GM time step (Wiens & Stockie, arxiv 1305.3976)."""
+"""GB300-native (sm_103a) IB-GM time step of Wiens & Stockie (arxiv 1305.3976).
+
+Python binding of the C ABI in include/ib_gb300.h: the functions below carry
+the C names and only marshal arguments; every step of the method runs in the
+CUDA kernels of libibgb300.so.  There is no CPU fallback: if the library is
+missing or cannot be built, the first call raises.
+
+PyTorch is optional plumbing: torch CUDA tensors may be passed wherever the ABI
+takes a device pointer, and by default a Grid works on torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+IB_OK, IB_ERR_ARG, IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_NONFINITE, IB_ERR_TIMEOUT, IB_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+IB_FP32, IB_FP64 = 0, 1
+IB_DELTA_PESKIN4, IB_DELTA_COS4 = 0, 1
+IB_FIELD_U, IB_FIELD_V, IB_FIELD_W, IB_FIELD_P, IB_FIELD_PSI, IB_FIELD_DIV = 1, 2, 4, 8, 16, 32
+FIELD_BITS = ("u", "v", "w", "p", "psi", "div")
+
+EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_read_fields", "ib_read_markers",
+           "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
+           "ib_cyclic_solve_lines", "ib_split_solve", "ib_profile_step", "ib_kernel_name")
+
+
+class ib_grid_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("H", C.c_double), ("rho", C.c_double),
+                ("mu", C.c_double), ("dt", C.c_double), ("chi", C.c_double), ("precision", C.c_int),
+                ("kernel", C.c_int), ("rotate_split", C.c_int), ("stream", C.c_void_p)]
+
+
+class ib_diag(C.Structure):
+    _fields_ = [("volume", C.c_double), ("div_l2", C.c_double), ("div_max", C.c_double),
+                ("kinetic", C.c_double), ("elastic", C.c_double), ("step", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "libibgb300.so")
+
+
+def lib():
+    """Load libibgb300.so (building it with nvcc first if it is stale)."""
+    global _lib
+    if _lib is None:
+        from . import _build
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, dp, ip, i64 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int64
+        L.ib_create_grid.argtypes = [C.POINTER(ib_grid_desc), C.POINTER(vp)]
+        L.ib_add_fiber.argtypes = [vp, dp, i64, ip, dp, dp, i64, ip, i64, C.POINTER(C.c_int32)]
+        L.ib_set_velocity.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.ib_step.argtypes = [vp, C.c_int]
+        L.ib_read_fields.argtypes = [vp, C.c_uint, vp, C.c_size_t, C.c_int]
+        L.ib_read_markers.argtypes = [vp, vp, i64, C.c_int]
+        L.ib_set_markers.argtypes = [vp, vp, i64, C.c_int]
+        L.ib_diagnostics.argtypes = [vp, C.POINTER(ib_diag)]
+        L.ib_destroy_grid.argtypes = [vp]
+        L.ib_error_string.argtypes = [C.c_int]
+        L.ib_error_string.restype = C.c_char_p
+        L.ib_last_error.argtypes = []
+        L.ib_last_error.restype = C.c_char_p
+        L.ib_cyclic_solve_lines.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_double, vp, vp, vp]
+        L.ib_split_solve.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp, vp, vp, vp]
+        L.ib_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+        L.ib_kernel_name.argtypes = [C.c_int]
+        L.ib_kernel_name.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("ib_error_string", "ib_last_error", "ib_kernel_name"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class IBError(RuntimeError):
+    def __init__(self, code, where):
+        L = lib()
+        super().__init__(f"{where}: {L.ib_error_string(code).decode()} ({code}): {L.ib_last_error().decode()}")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != IB_OK:
+        raise IBError(rc, where)
+
+
+# ---------------------------------------------------------------------------
+# pointer helpers: numpy arrays are host memory, torch CUDA tensors device
+
+
+def _is_torch_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x):
+    if _is_torch_cuda(x) or (hasattr(x, "data_ptr") and hasattr(x, "is_cuda")):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+    return C.c_void_p(x.ctypes.data), 0
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+
+
+def ib_create_grid(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision=IB_FP32,
+                   kernel=IB_DELTA_PESKIN4, rotate_split=1, stream="current"):
+    d = ib_grid_desc()
+    d.dim = dim
+    n = [int(n)] * dim if np.isscalar(n) else list(n)
+    n = n + [1] * (3 - len(n))
+    d.n[0], d.n[1], d.n[2] = n
+    d.H, d.rho, d.mu, d.dt, d.chi = H, rho, mu, dt, chi
+    d.precision, d.kernel, d.rotate_split = precision, kernel, int(rotate_split)
+    d.stream = _current_stream() if stream == "current" else stream
+    h = C.c_void_p()
+    _check(lib().ib_create_grid(C.byref(d), C.byref(h)), "ib_create_grid")
+    return h
+
+
+def ib_add_fiber(g, X0, edges, kappa, rest_len=None, tris=None):
+    X0 = np.ascontiguousarray(X0, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    r = None if rest_len is None else np.ascontiguousarray(rest_len, dtype=np.float64)
+    t = None if tris is None else np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    fid = C.c_int32()
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    _check(lib().ib_add_fiber(g, X0.ctypes.data_as(dp), X0.shape[0], e.ctypes.data_as(ip), k.ctypes.data_as(dp),
+                              None if r is None else r.ctypes.data_as(dp), e.shape[0],
+                              None if t is None else t.ctypes.data_as(ip), 0 if t is None else t.shape[0],
+                              C.byref(fid)), "ib_add_fiber")
+    return fid.value
+
+
+def ib_set_velocity(g, comp, src):
+    p, dev = _ptr(src)
+    _check(lib().ib_set_velocity(g, comp, p, dev), "ib_set_velocity")
+
+
+def ib_step(g, n_steps=1):
+    _check(lib().ib_step(g, int(n_steps)), "ib_step")
+
+
+def ib_read_fields(g, field_mask, dst):
+    p, dev = _ptr(dst)
+    nbytes = dst.numel() * dst.element_size() if dev else dst.nbytes
+    _check(lib().ib_read_fields(g, field_mask, p, nbytes, dev), "ib_read_fields")
+    return dst
+
+
+def ib_read_markers(g, dst):
+    p, dev = _ptr(dst)
+    n = dst.shape[0]
+    _check(lib().ib_read_markers(g, p, n, dev), "ib_read_markers")
+    return dst
+
+
+def ib_set_markers(g, src):
+    p, dev = _ptr(src)
+    _check(lib().ib_set_markers(g, p, src.shape[0], dev), "ib_set_markers")
+
+
+def ib_diagnostics(g, check=True):
+    d = ib_diag()
+    rc = lib().ib_diagnostics(g, C.byref(d))
+    if check:
+        _check(rc, "ib_diagnostics")
+    return {k: getattr(d, k) for k, _ in ib_diag._fields_}, rc
+
+
+def ib_destroy_grid(g):
+    _check(lib().ib_destroy_grid(g), "ib_destroy_grid")
+
+
+def ib_cyclic_solve_lines(precision, dim, n, axis, r, src, dst, stream="current"):
+    na = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    s = _current_stream() if stream == "current" else stream
+    _check(lib().ib_cyclic_solve_lines(precision, dim, na, axis, float(r), _ptr(src)[0], _ptr(dst)[0],
+                                       C.c_void_p(s)), "ib_cyclic_solve_lines")
+
+
+def ib_split_solve(precision, dim, n, r, f, psi, stream="current"):
+    na = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    ra = (C.c_double * 3)(*(list(r) + [0.0] * (3 - len(r))))
+    s = _current_stream() if stream == "current" else stream
+    _check(lib().ib_split_solve(precision, dim, na, ra, _ptr(f)[0], _ptr(psi)[0], C.c_void_p(s)), "ib_split_solve")
+
+
+def ib_profile_step(g, n_steps):
+    ms = (C.c_float * 16)()
+    nk = C.c_int()
+    _check(lib().ib_profile_step(g, int(n_steps), ms, 16, C.byref(nk)), "ib_profile_step")
+    return {lib().ib_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+
+
+class Grid:
+    """An ib_grid_t with numpy/torch conveniences (argument marshalling only)."""
+
+    def __init__(self, dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision="fp32",
+                 kernel="peskin4", rotate_split=True, stream="current"):
+        self.dim = dim
+        self.n = [int(n)] * dim if np.isscalar(n) else list(n)[:dim]
+        self.precision = IB_FP32 if precision in ("fp32", IB_FP32) else IB_FP64
+        self.dtype = np.float32 if self.precision == IB_FP32 else np.float64
+        k = {"peskin4": IB_DELTA_PESKIN4, "cos4": IB_DELTA_COS4}.get(kernel, kernel)
+        self.h = ib_create_grid(dim, self.n, H, rho, mu, dt, chi, self.precision, k, rotate_split, stream)
+        self.n_markers = 0
+
+    @property
+    def field_shape(self):
+        return tuple(reversed(self.n))
+
+    def add_fiber(self, X, edges, kappa, rest=None, tris=None):
+        fid = ib_add_fiber(self.h, X, edges, kappa, rest, tris)
+        self.n_markers += np.asarray(X).shape[0]
+        return fid
+
+    def set_velocity(self, u):
+        for c in range(self.dim):
+            src = u[c]
+            if not _is_torch_cuda(src):
+                src = np.ascontiguousarray(src, dtype=self.dtype)
+            ib_set_velocity(self.h, c, src)
+
+    def step(self, n=1):
+        ib_step(self.h, n)
+
+    def fields(self, names=FIELD_BITS):
+        """Host copies of the named fields ('u', 'v', 'w', 'p', 'psi', 'div')."""
+        out = {}
+        for name in names:
+            b = FIELD_BITS.index(name)
+            if b == 2 and self.dim == 2:
+                continue
+            arr = np.empty(self.field_shape, dtype=self.dtype)
+            ib_read_fields(self.h, 1 << b, arr)
+            out[name] = arr
+        return out
+
+    def velocity(self):
+        f = self.fields(("u", "v", "w")[:self.dim])
+        return np.stack([f[k] for k in ("u", "v", "w")[:self.dim]])
+
+    def markers(self):
+        X = np.empty((self.n_markers, self.dim), dtype=np.float64)
+        return ib_read_markers(self.h, X)
+
+    def set_markers(self, X):
+        ib_set_markers(self.h, np.ascontiguousarray(X, dtype=np.float64))
+
+    def diagnostics(self, check=True):
+        return ib_diagnostics(self.h, check)[0]
+
+    def profile(self, n_steps=1):
+        return ib_profile_step(self.h, n_steps)
+
+    def close(self):
+        if self.h:
+            ib_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

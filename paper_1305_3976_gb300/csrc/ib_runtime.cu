@@ -1,0 +1,761 @@
+// Host runtime and C ABI of the sm_103a IB-GM step (include/ib_gb300.h).
+//
+// One ib_grid_t owns, on the current device:
+//   fields  (precision T): u[d], p, psi, Nold[d] = N(u^{n-1}), div = D.u^n,
+//           scr[d] (spread force f -> momentum increment R -> sweep results;
+//           zero between steps), all in one allocation;
+//   markers (FP64 SoA): X, Xh = X^{n+1/2}, U = U^n, Uold = U^{n-1}, G, plus
+//           the force connections as CSR by marker and as an edge list;
+//   line-solve tables: lam^k (k = 0..n_a) per axis for the momentum operator
+//           (r = mu dt / (2 rho h_a^2)) and the psi operator (r = 1 / h_a^2).
+// A step is 10 launches in 3D (8 in 2D): interp, force, spread, rhs, d
+// momentum sweeps, d psi sweeps.  Steps after the first replay a CUDA graph
+// (one per split-order phase) on a library-owned stream that is ordered
+// against the caller's stream with events.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ib_gb300.h"
+#include "ib_internal.cuh"
+
+using namespace ibg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define IB_CUDA(call)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(IB_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// lam, c and lam^k of the cyclic operator (1 + 2r) I - r (S + S^{-1}) =
+// c (I - lam S)(I - lam S^{-1}); computed in FP64 on the host.
+struct HostCoef {
+  double lam, inv_c, inv_1m;
+  std::vector<double> pw;
+};
+HostCoef make_coef(int n, double r) {
+  HostCoef h;
+  const double lam = 2.0 * r / (1.0 + 2.0 * r + sqrt(1.0 + 4.0 * r));
+  h.lam = lam;
+  h.inv_c = 2.0 / (1.0 + 2.0 * r + sqrt(1.0 + 4.0 * r));  // 1 / c, c = r / lam
+  h.pw.resize(n + 1);
+  double p = 1.0;
+  for (int k = 0; k <= n; ++k) {
+    h.pw[k] = p;
+    p *= lam;
+  }
+  h.inv_1m = 1.0 / (1.0 - h.pw[n]);
+  return h;
+}
+
+// device copy of a coefficient table in both precisions
+struct DevCoef {
+  void *mem = nullptr;
+  LineCoef<float> f;
+  LineCoef<double> d;
+};
+int upload_coef(const HostCoef &h, DevCoef &out, cudaStream_t s) {
+  const int m = (int)h.pw.size();
+  size_t bytes = m * sizeof(double) + m * sizeof(float) + 64;
+  IB_CUDA(cudaMalloc(&out.mem, bytes));
+  double *pd = (double *)out.mem;
+  float *pf = (float *)(pd + m);
+  std::vector<float> hf(m);
+  for (int k = 0; k < m; ++k) hf[k] = (float)h.pw[k];
+  IB_CUDA(cudaMemcpyAsync(pd, h.pw.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+  IB_CUDA(cudaMemcpyAsync(pf, hf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
+  IB_CUDA(cudaStreamSynchronize(s));
+  out.d = LineCoef<double>{pd, h.lam, h.inv_c, h.inv_1m};
+  out.f = LineCoef<float>{pf, (float)h.lam, (float)h.inv_c, (float)h.inv_1m};
+  return IB_OK;
+}
+
+template <typename T>
+const LineCoef<T> &coef_of(const DevCoef &c);
+template <>
+const LineCoef<float> &coef_of<float>(const DevCoef &c) { return c.f; }
+template <>
+const LineCoef<double> &coef_of<double>(const DevCoef &c) { return c.d; }
+
+// process-wide cache for the stand-alone line-solve entry points
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, double>, DevCoef> g_cache;  // (device, n, r)
+
+int cached_coef(int n, double r, cudaStream_t s, DevCoef **out) {
+  int dev = 0;
+  IB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto key = std::make_tuple(dev, n, r);
+  auto it = g_cache.find(key);
+  if (it == g_cache.end()) {
+    DevCoef c;
+    cudaStream_t tmp;
+    IB_CUDA(cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking));
+    int rc = upload_coef(make_coef(n, r), c, tmp);
+    cudaStreamDestroy(tmp);
+    if (rc != IB_OK) return rc;
+    it = g_cache.emplace(key, c).first;
+  }
+  *out = &it->second;
+  (void)s;
+  return IB_OK;
+}
+
+}  // namespace
+
+const char *ib_kernel_name(int slot);
+
+struct ib_grid_s {
+  ib_grid_desc desc;
+  int dim = 0, prec = 0;
+  int n[3] = {1, 1, 1};
+  long long cells = 0;
+  double h[3] = {1, 1, 1};
+  size_t esz = 4;
+  void *fields = nullptr;
+  void *u[3] = {}, *p = nullptr, *psi = nullptr, *Nold[3] = {}, *div = nullptr, *scr[3] = {};
+  DevCoef coef[2][3];  // [0: momentum, 1: psi][axis]
+
+  // markers
+  std::vector<double> hX;       // [nm][dim]
+  std::vector<int32_t> hE;      // [ne][2] global indices
+  std::vector<double> hK, hR;   // [ne]
+  std::vector<int32_t> hT;      // [nt][3] global indices
+  int64_t nm = 0, ne = 0, nt = 0;
+  int nfibers = 0;
+  bool markers_uploaded = false;
+  void *mk = nullptr;           // one allocation for all marker data
+  double *X[3] = {}, *Xh[3] = {}, *U[3] = {}, *Uold[3] = {}, *G[3] = {};
+  int64_t *row = nullptr;
+  int32_t *col = nullptr, *edges = nullptr, *tris = nullptr;
+  double *kap = nullptr, *rest = nullptr, *ekap = nullptr, *erest = nullptr;
+  double *acc = nullptr;        // diagnostics accumulators (device)
+  double *stage = nullptr;      // [nm][dim] staging buffer for marker I/O
+
+  int64_t step = 0;
+  bool div_valid = false;
+  cudaStream_t s = nullptr;     // library stream
+  cudaStream_t user = nullptr;  // caller stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+template <typename T>
+int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+  const int d = g->dim;
+  int order[3];
+  for (int i = 0; i < d; ++i) order[i] = (i + phase) % d;
+  auto mark = [&](int slot) -> int {
+    if (ev) IB_CUDA(cudaEventRecord(ev[slot], g->s));
+    return IB_OK;
+  };
+  int rc;
+  // markers
+  MarkerArgs m;
+  memset(&m, 0, sizeof(m));
+  for (int a = 0; a < 3; ++a) {
+    m.X[a] = g->X[a];
+    m.Xh[a] = g->Xh[a];
+    m.U[a] = g->U[a];
+    m.Uold[a] = g->Uold[a];
+    m.G[a] = g->G[a];
+    m.inv_h[a] = 1.0 / g->h[a];
+    m.n[a] = g->n[a];
+  }
+  m.row = g->row;
+  m.col = g->col;
+  m.kap = g->kap;
+  m.rest = g->rest;
+  m.nm = g->nm;
+  m.dt = g->desc.dt;
+  m.H = g->desc.H;
+  m.inv_vol = 1.0;
+  for (int a = 0; a < d; ++a) m.inv_vol /= g->h[a];
+  m.dim = d;
+  m.kernel = g->desc.kernel;
+  m.first = first ? 1 : 0;
+  const T *uc[3] = {(const T *)g->u[0], (const T *)g->u[1], (const T *)g->u[2]};
+  T *sc[3] = {(T *)g->scr[0], (T *)g->scr[1], (T *)g->scr[2]};
+  if ((rc = mark(0))) return rc;
+  IB_CUDA(launch_interp<T>(m, uc, g->s));
+  if ((rc = mark(1))) return rc;
+  IB_CUDA(launch_force(m, g->s));
+  if ((rc = mark(2))) return rc;
+  IB_CUDA(launch_spread<T>(m, sc, g->s));
+  if ((rc = mark(3))) return rc;
+  // Steps 3a-3b
+  RhsArgs<T> ra;
+  memset(&ra, 0, sizeof(ra));
+  for (int a = 0; a < 3; ++a) {
+    ra.u[a] = uc[a];
+    ra.Nold[a] = (T *)g->Nold[a];
+    ra.scr[a] = sc[a];
+    ra.inv_h[a] = (T)(1.0 / g->h[a]);
+    ra.inv_h2[a] = (T)(1.0 / (g->h[a] * g->h[a]));
+    ra.n[a] = g->n[a];
+  }
+  ra.p = (const T *)g->p;
+  ra.psi = (const T *)g->psi;
+  ra.mu = (T)g->desc.mu;
+  ra.inv_rho = (T)(1.0 / g->desc.rho);
+  ra.dt = (T)g->desc.dt;
+  ra.first = first ? 1 : 0;
+  IB_CUDA(launch_rhs<T>(d, ra, g->s));
+  if ((rc = mark(4))) return rc;
+  // Steps 3c-3d (+ z): increment-form Douglas sweeps on the scratch fields
+  SweepArgs<T> sa;
+  memset(&sa, 0, sizeof(sa));
+  for (int a = 0; a < 3; ++a) {
+    sa.f[a] = sc[a];
+    sa.u[a] = uc[a];
+    sa.uo[a] = (T *)g->u[a];
+    sa.inv_h[a] = (T)(1.0 / g->h[a]);
+    sa.n[a] = g->n[a];
+  }
+  sa.p = (T *)g->p;
+  sa.div = (T *)g->div;
+  sa.pro_scale = (T)(-g->desc.rho / g->desc.dt);
+  sa.chi_mu_half = (T)(0.5 * g->desc.chi * g->desc.mu);
+  sa.dim = d;
+  for (int st = 0; st < d; ++st) {
+    const int ax = order[st];
+    sa.co = coef_of<T>(g->coef[0][ax]);
+    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, st == d - 1 ? EPI_ADDU : EPI_STORE, d, sa, g->s));
+    if ((rc = mark(5 + st))) return rc;
+  }
+  // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
+  // last sweeps
+  sa.f[0] = sa.f[1] = sa.f[2] = (T *)g->psi;
+  for (int st = 0; st < d; ++st) {
+    const int ax = order[st];
+    sa.co = coef_of<T>(g->coef[1][ax]);
+    const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
+    const int epi = st == d - 1 ? EPI_P : EPI_STORE;
+    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s));
+    if ((rc = mark(8 + st))) return rc;
+  }
+  return IB_OK;
+}
+
+int enqueue_step(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+  return g->prec == IB_FP32 ? enqueue_step_t<float>(g, first, phase, ev)
+                            : enqueue_step_t<double>(g, first, phase, ev);
+}
+
+int ensure_div(ib_grid_s *g) {
+  if (g->div_valid) return IB_OK;
+  if (g->prec == IB_FP32) {
+    const float *uc[3] = {(const float *)g->u[0], (const float *)g->u[1], (const float *)g->u[2]};
+    const float ih[3] = {(float)(1.0 / g->h[0]), (float)(1.0 / g->h[1]), (float)(1.0 / g->h[2])};
+    IB_CUDA(launch_divergence<float>(g->dim, uc, (float *)g->div, g->n, ih, g->s));
+  } else {
+    const double *uc[3] = {(const double *)g->u[0], (const double *)g->u[1], (const double *)g->u[2]};
+    const double ih[3] = {1.0 / g->h[0], 1.0 / g->h[1], 1.0 / g->h[2]};
+    IB_CUDA(launch_divergence<double>(g->dim, uc, (double *)g->div, g->n, ih, g->s));
+  }
+  g->div_valid = true;
+  return IB_OK;
+}
+
+// Build the device marker arrays and the CSR neighbour lists (once, before the
+// first step).
+int upload_markers(ib_grid_s *g) {
+  if (g->markers_uploaded) return IB_OK;
+  const int d = g->dim;
+  const int64_t nm = g->nm, ne = g->ne, nt = g->nt;
+  std::vector<int64_t> row(nm + 1, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    row[g->hE[2 * e] + 1]++;
+    row[g->hE[2 * e + 1] + 1]++;
+  }
+  for (int64_t a = 0; a < nm; ++a) row[a + 1] += row[a];
+  std::vector<int32_t> col(2 * ne);
+  std::vector<double> kap(2 * ne), rest(2 * ne);
+  std::vector<int64_t> fill(row.begin(), row.end() - 1);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t a = g->hE[2 * e], b = g->hE[2 * e + 1];
+    int64_t pa = fill[a]++, pb = fill[b]++;
+    col[pa] = b;
+    col[pb] = a;
+    kap[pa] = kap[pb] = g->hK[e];
+    rest[pa] = rest[pb] = g->hR[e];
+  }
+  std::vector<double> soa(nm * d);
+  for (int64_t k = 0; k < nm; ++k)
+    for (int a = 0; a < d; ++a) soa[a * nm + k] = g->hX[k * d + a];
+  // layout: 5 d nm doubles | row | col | kap | rest | edges | ekap | erest | tris | acc
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_m = take(sizeof(double) * 5 * d * (nm + 1));
+  const size_t o_row = take(sizeof(int64_t) * (nm + 1));
+  const size_t o_col = take(sizeof(int32_t) * (2 * ne + 1));
+  const size_t o_kap = take(sizeof(double) * (2 * ne + 1));
+  const size_t o_rest = take(sizeof(double) * (2 * ne + 1));
+  const size_t o_e = take(sizeof(int32_t) * (2 * ne + 1));
+  const size_t o_ek = take(sizeof(double) * (ne + 1));
+  const size_t o_er = take(sizeof(double) * (ne + 1));
+  const size_t o_t = take(sizeof(int32_t) * (3 * nt + 1));
+  const size_t o_acc = take(sizeof(double) * 8);
+  const size_t o_stage = take(sizeof(double) * (nm * d + 1));
+  if (cudaMalloc(&g->mk, off) != cudaSuccess) return fail(IB_ERR_OOM, "marker allocation of %zu bytes failed", off);
+  char *base = (char *)g->mk;
+  double *md = (double *)(base + o_m);
+  for (int a = 0; a < 3; ++a) {
+    const int aa = a < d ? a : d - 1;
+    g->X[a] = md + (0 * d + aa) * nm;
+    g->Xh[a] = md + (1 * d + aa) * nm;
+    g->U[a] = md + (2 * d + aa) * nm;
+    g->Uold[a] = md + (3 * d + aa) * nm;
+    g->G[a] = md + (4 * d + aa) * nm;
+  }
+  g->row = (int64_t *)(base + o_row);
+  g->col = (int32_t *)(base + o_col);
+  g->kap = (double *)(base + o_kap);
+  g->rest = (double *)(base + o_rest);
+  g->edges = (int32_t *)(base + o_e);
+  g->ekap = (double *)(base + o_ek);
+  g->erest = (double *)(base + o_er);
+  g->tris = (int32_t *)(base + o_t);
+  g->acc = (double *)(base + o_acc);
+  g->stage = (double *)(base + o_stage);
+  IB_CUDA(cudaMemsetAsync(g->mk, 0, off, g->s));
+  if (nm) IB_CUDA(cudaMemcpyAsync(g->X[0], soa.data(), sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
+  IB_CUDA(cudaMemcpyAsync(g->row, row.data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, g->s));
+  if (ne) {
+    IB_CUDA(cudaMemcpyAsync(g->col, col.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->edges, g->hE.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->ekap, g->hK.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->erest, g->hR.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
+  }
+  if (nt) IB_CUDA(cudaMemcpyAsync(g->tris, g->hT.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));  // host vectors above go out of scope
+  g->markers_uploaded = true;
+  return IB_OK;
+}
+
+int enter(ib_grid_s *g) {
+  IB_CUDA(cudaEventRecord(g->ev_in, g->user));
+  IB_CUDA(cudaStreamWaitEvent(g->s, g->ev_in, 0));
+  return IB_OK;
+}
+int leave(ib_grid_s *g) {
+  IB_CUDA(cudaEventRecord(g->ev_out, g->s));
+  IB_CUDA(cudaStreamWaitEvent(g->user, g->ev_out, 0));
+  return IB_OK;
+}
+
+int get_graph(ib_grid_s *g, int phase) {
+  if (g->graph[phase]) return IB_OK;
+  cudaGraph_t graph;
+  IB_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step(g, false, phase, nullptr);
+  cudaError_t e = cudaStreamEndCapture(g->s, &graph);
+  if (rc != IB_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(IB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g->graph[phase], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(IB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return IB_OK;
+}
+
+int prepare(ib_grid_s *g) {
+  int rc = upload_markers(g);
+  if (rc) return rc;
+  if ((rc = ensure_div(g))) return rc;
+  // capture the step graph of every split-order phase up front so that no
+  // instantiation happens between later steps
+  const int phases = g->desc.rotate_split ? g->dim : 1;
+  for (int ph = 0; ph < phases; ++ph)
+    if ((rc = get_graph(g, ph))) return rc;
+  return IB_OK;
+}
+
+bool valid_n(int n) { return n >= 8 && n <= 512; }
+
+}  // namespace
+
+extern "C" {
+
+const char *ib_error_string(int code) {
+  switch (code) {
+    case IB_OK: return "ok";
+    case IB_ERR_ARG: return "invalid argument";
+    case IB_ERR_OOM: return "out of memory";
+    case IB_ERR_CUDA: return "CUDA error";
+    case IB_ERR_NONFINITE: return "non-finite value in the state";
+    case IB_ERR_TIMEOUT: return "device wait timed out";
+    case IB_ERR_STATE: return "call not allowed in the current state";
+    default: return "unknown error";
+  }
+}
+
+const char *ib_last_error(void) { return g_last_error.c_str(); }
+
+int ib_create_grid(const ib_grid_desc *desc, ib_grid_t *out) {
+  if (!desc || !out) return fail(IB_ERR_ARG, "null argument");
+  *out = nullptr;
+  const ib_grid_desc &D = *desc;
+  if (D.dim != 2 && D.dim != 3) return fail(IB_ERR_ARG, "dim must be 2 or 3");
+  for (int a = 0; a < D.dim; ++a)
+    if (!valid_n(D.n[a])) return fail(IB_ERR_ARG, "n[%d] = %d outside [8, 512]", a, D.n[a]);
+  if (!(D.H > 0) || !(D.rho > 0) || !(D.mu >= 0) || !(D.dt > 0) || !(D.chi >= 0))
+    return fail(IB_ERR_ARG, "H, rho, dt must be > 0 and mu, chi >= 0");
+  if (D.precision != IB_FP32 && D.precision != IB_FP64) return fail(IB_ERR_ARG, "precision");
+  if (D.kernel != IB_DELTA_PESKIN4 && D.kernel != IB_DELTA_COS4) return fail(IB_ERR_ARG, "kernel");
+  ib_grid_s *g = new ib_grid_s();
+  g->desc = D;
+  g->dim = D.dim;
+  g->prec = D.precision;
+  g->esz = D.precision == IB_FP32 ? 4 : 8;
+  for (int a = 0; a < D.dim; ++a) {
+    g->n[a] = D.n[a];
+    g->h[a] = D.H / D.n[a];
+  }
+  g->cells = (long long)g->n[0] * g->n[1] * g->n[2];
+  g->user = (cudaStream_t)D.stream;
+  auto cleanup = [&](int rc) {
+    ib_destroy_grid(g);
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(IB_ERR_CUDA, "stream/event creation failed"));
+  const int d = g->dim;
+  const int nf = 3 * d + 3;
+  const size_t fbytes = ((size_t)g->cells * g->esz + 255) / 256 * 256;
+  if (cudaMalloc(&g->fields, fbytes * nf) != cudaSuccess)
+    return cleanup(fail(IB_ERR_OOM, "field allocation of %zu bytes failed", fbytes * nf));
+  char *b = (char *)g->fields;
+  int slot = 0;
+  for (int a = 0; a < d; ++a) g->u[a] = b + fbytes * slot++;
+  g->p = b + fbytes * slot++;
+  g->psi = b + fbytes * slot++;
+  for (int a = 0; a < d; ++a) g->Nold[a] = b + fbytes * slot++;
+  g->div = b + fbytes * slot++;
+  for (int a = 0; a < d; ++a) g->scr[a] = b + fbytes * slot++;
+  for (int a = d; a < 3; ++a) {  // unused third component aliases the second
+    g->u[a] = g->u[d - 1];
+    g->Nold[a] = g->Nold[d - 1];
+    g->scr[a] = g->scr[d - 1];
+  }
+  if (cudaMemsetAsync(g->fields, 0, fbytes * nf, g->s) != cudaSuccess)
+    return cleanup(fail(IB_ERR_CUDA, "memset"));
+  const double amom = D.mu * D.dt / (2.0 * D.rho);
+  for (int a = 0; a < d; ++a) {
+    int rc = upload_coef(make_coef(g->n[a], amom / (g->h[a] * g->h[a])), g->coef[0][a], g->s);
+    if (rc == IB_OK) rc = upload_coef(make_coef(g->n[a], 1.0 / (g->h[a] * g->h[a])), g->coef[1][a], g->s);
+    if (rc != IB_OK) return cleanup(rc);
+  }
+  if (cudaStreamSynchronize(g->s) != cudaSuccess) return cleanup(fail(IB_ERR_CUDA, "sync"));
+  *out = g;
+  return IB_OK;
+}
+
+int ib_destroy_grid(ib_grid_t g) {
+  if (!g) return IB_OK;
+  if (g->s) cudaStreamSynchronize(g->s);
+  for (int i = 0; i < 3; ++i)
+    if (g->graph[i]) cudaGraphExecDestroy(g->graph[i]);
+  for (int k = 0; k < 2; ++k)
+    for (int a = 0; a < 3; ++a)
+      if (g->coef[k][a].mem) cudaFree(g->coef[k][a].mem);
+  if (g->fields) cudaFree(g->fields);
+  if (g->mk) cudaFree(g->mk);
+  if (g->ev_in) cudaEventDestroy(g->ev_in);
+  if (g->ev_out) cudaEventDestroy(g->ev_out);
+  if (g->s) cudaStreamDestroy(g->s);
+  delete g;
+  return IB_OK;
+}
+
+int ib_add_fiber(ib_grid_t g, const double *X0, int64_t n_markers, const int32_t *edges, const double *kappa,
+                 const double *rest_len, int64_t n_edges, const int32_t *tris, int64_t n_tris,
+                 int32_t *fiber_id_out) {
+  if (!g) return fail(IB_ERR_ARG, "null grid");
+  if (g->step != 0 || g->markers_uploaded) return fail(IB_ERR_STATE, "fibers can only be added before the first step");
+  if (n_markers < 0 || n_edges < 0 || n_tris < 0) return fail(IB_ERR_ARG, "negative count");
+  if (n_markers > 0 && !X0) return fail(IB_ERR_ARG, "null X0");
+  if (n_edges > 0 && (!edges || !kappa)) return fail(IB_ERR_ARG, "null edges or kappa");
+  if (g->nm + n_markers > (int64_t)0x7fffffff) return fail(IB_ERR_ARG, "too many markers");
+  const int d = g->dim;
+  for (int64_t i = 0; i < n_markers * d; ++i)
+    if (!isfinite(X0[i])) return fail(IB_ERR_NONFINITE, "non-finite marker position");
+  for (int64_t e = 0; e < 2 * n_edges; ++e)
+    if (edges[e] < 0 || edges[e] >= n_markers) return fail(IB_ERR_ARG, "edge index %d out of range", edges[e]);
+  if (d == 3)
+    for (int64_t t = 0; t < 3 * n_tris; ++t)
+      if (!tris || tris[t] < 0 || tris[t] >= n_markers) return fail(IB_ERR_ARG, "triangle index out of range");
+  const int32_t off = (int32_t)g->nm;
+  g->hX.insert(g->hX.end(), X0, X0 + n_markers * d);
+  for (int64_t e = 0; e < n_edges; ++e) {
+    g->hE.push_back(edges[2 * e] + off);
+    g->hE.push_back(edges[2 * e + 1] + off);
+    g->hK.push_back(kappa[e]);
+    g->hR.push_back(rest_len ? rest_len[e] : 0.0);
+  }
+  if (d == 3)
+    for (int64_t t = 0; t < 3 * n_tris; ++t) g->hT.push_back(tris[t] + off);
+  g->nm += n_markers;
+  g->ne += n_edges;
+  if (d == 3) g->nt += n_tris;
+  if (fiber_id_out) *fiber_id_out = g->nfibers;
+  g->nfibers++;
+  return IB_OK;
+}
+
+int ib_set_velocity(ib_grid_t g, int comp, const void *src, int on_device) {
+  if (!g || !src) return fail(IB_ERR_ARG, "null argument");
+  if (comp < 0 || comp >= g->dim) return fail(IB_ERR_ARG, "component %d", comp);
+  if (g->step != 0) return fail(IB_ERR_STATE, "velocity can only be set before the first step");
+  int rc = enter(g);
+  if (rc) return rc;
+  IB_CUDA(cudaMemcpyAsync(g->u[comp], src, g->cells * g->esz,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
+  if (!on_device) IB_CUDA(cudaStreamSynchronize(g->s));
+  g->div_valid = false;
+  return leave(g);
+}
+
+int ib_step(ib_grid_t g, int n_steps) {
+  if (!g) return fail(IB_ERR_ARG, "null grid");
+  if (n_steps < 0) return fail(IB_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return IB_OK;
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((rc = prepare(g))) return rc;
+  for (int i = 0; i < n_steps; ++i) {
+    if (g->step == 0) {
+      if ((rc = enqueue_step(g, true, 0, nullptr))) return rc;
+    } else {
+      const int phase = g->desc.rotate_split ? (int)(g->step % g->dim) : 0;
+      if ((rc = get_graph(g, phase))) return rc;
+      IB_CUDA(cudaGraphLaunch(g->graph[phase], g->s));
+    }
+    g->step++;
+  }
+  return leave(g);
+}
+
+int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels, int *n_kernels) {
+  if (!g || !kernel_ms || n_steps < 0) return fail(IB_ERR_ARG, "bad argument");
+  const int nslots = 11;  // 3 marker + rhs + 3 momentum + 3 psi + end mark
+  cudaEvent_t ev[nslots + 1];
+  for (int i = 0; i <= nslots; ++i) IB_CUDA(cudaEventCreate(&ev[i]));
+  std::vector<double> tot(nslots, 0.0);
+  int rc = enter(g);
+  if (!rc) rc = prepare(g);
+  for (int i = 0; i < n_steps && !rc; ++i) {
+    const int phase = g->desc.rotate_split ? (int)(g->step % g->dim) : 0;
+    // slots of kernels that do not run in this configuration keep equal events
+    for (int k = 0; k <= nslots; ++k) cudaEventRecord(ev[k], g->s);
+    rc = enqueue_step(g, g->step == 0, phase, ev);
+    if (rc) break;
+    cudaEventRecord(ev[nslots], g->s);
+    if (cudaEventSynchronize(ev[nslots]) != cudaSuccess) {
+      rc = fail(IB_ERR_CUDA, "profiling sync");
+      break;
+    }
+    // marks: 0 before interp, 1 after interp, 2 after force, 3 after spread,
+    // 4 after rhs, 5 + s after the s-th momentum sweep, 8 + s after the s-th
+    // psi sweep (s in split order); slots of a 2D step leave equal marks
+    float ms;
+    const int last_m = 5 + g->dim - 1, last_p = 8 + g->dim - 1;
+    for (int k = 0; k < 4; ++k) {
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      tot[k] += ms;
+    }
+    for (int q = 0; q < g->dim; ++q) {
+      cudaEventElapsedTime(&ms, ev[4 + q], ev[5 + q]);
+      tot[4 + q] += ms;
+    }
+    for (int q = 0; q < g->dim; ++q) {
+      cudaEventElapsedTime(&ms, q == 0 ? ev[last_m] : ev[7 + q], ev[8 + q]);
+      tot[7 + q] += ms;
+    }
+    (void)last_p;
+    g->step++;
+  }
+  for (int i = 0; i <= nslots; ++i) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  const int nk = 10;
+  for (int k = 0; k < nk && k < max_kernels; ++k) kernel_ms[k] = (float)tot[k];
+  if (n_kernels) *n_kernels = nk < max_kernels ? nk : max_kernels;
+  return leave(g);
+}
+
+const char *ib_kernel_name(int slot) {
+  // sweeps are numbered by their position in the step's split order
+  static const char *names[] = {"interp",      "force",       "spread",      "rhs",         "mom_sweep_1",
+                                "mom_sweep_2", "mom_sweep_3", "psi_sweep_1", "psi_sweep_2", "psi_sweep_3"};
+  return (slot >= 0 && slot < 10) ? names[slot] : "";
+}
+
+int ib_read_fields(ib_grid_t g, unsigned field_mask, void *dst, size_t bytes, int dst_on_device) {
+  if (!g || !dst) return fail(IB_ERR_ARG, "null argument");
+  void *src[6] = {g->u[0], g->u[1], g->dim == 3 ? g->u[2] : nullptr, g->p, g->psi, g->div};
+  size_t need = 0;
+  for (int b = 0; b < 6; ++b)
+    if (field_mask & (1u << b)) {
+      if (!src[b]) return fail(IB_ERR_ARG, "field bit %d not present in %dD", b, g->dim);
+      need += g->cells * g->esz;
+    }
+  if (need != bytes) return fail(IB_ERR_ARG, "bytes = %zu, fields need %zu", bytes, need);
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((field_mask & IB_FIELD_DIV) && (rc = ensure_div(g))) return rc;
+  char *o = (char *)dst;
+  for (int b = 0; b < 6; ++b)
+    if (field_mask & (1u << b)) {
+      IB_CUDA(cudaMemcpyAsync(o, src[b], g->cells * g->esz,
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->s));
+      o += g->cells * g->esz;
+    }
+  if (!dst_on_device) IB_CUDA(cudaStreamSynchronize(g->s));
+  return leave(g);
+}
+
+int ib_read_markers(ib_grid_t g, double *X, int64_t n, int dst_on_device) {
+  if (!g || (!X && n)) return fail(IB_ERR_ARG, "null argument");
+  if (n != g->nm) return fail(IB_ERR_ARG, "n = %lld, grid has %lld markers", (long long)n, (long long)g->nm);
+  if (n == 0) return IB_OK;
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((rc = upload_markers(g))) return rc;
+  const int d = g->dim;
+  // SoA on the device -> [n][dim] staging -> caller
+  IB_CUDA(launch_markers_layout(g->stage, g->X, n, d, 0, g->s));
+  IB_CUDA(cudaMemcpyAsync(X, g->stage, sizeof(double) * n * d,
+                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->s));
+  if (!dst_on_device) IB_CUDA(cudaStreamSynchronize(g->s));
+  return leave(g);
+}
+
+int ib_set_markers(ib_grid_t g, const double *X, int64_t n, int src_on_device) {
+  if (!g || (!X && n)) return fail(IB_ERR_ARG, "null argument");
+  if (n != g->nm) return fail(IB_ERR_ARG, "n = %lld, grid has %lld markers", (long long)n, (long long)g->nm);
+  if (n == 0) return IB_OK;
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((rc = upload_markers(g))) return rc;
+  const int d = g->dim;
+  IB_CUDA(cudaMemcpyAsync(g->stage, X, sizeof(double) * n * d,
+                          src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
+  IB_CUDA(launch_markers_layout(g->stage, g->X, n, d, 1, g->s));
+  if (!src_on_device) IB_CUDA(cudaStreamSynchronize(g->s));
+  return leave(g);
+}
+
+int ib_diagnostics(ib_grid_t g, ib_diag *out) {
+  if (!g || !out) return fail(IB_ERR_ARG, "null argument");
+  int rc = enter(g);
+  if (!rc) rc = prepare(g);
+  if (rc) return rc;
+  IB_CUDA(cudaMemsetAsync(g->acc, 0, 8 * sizeof(double), g->s));
+  if (g->prec == IB_FP32) {
+    const float *uc[3] = {(const float *)g->u[0], (const float *)g->u[1], (const float *)g->u[2]};
+    IB_CUDA(launch_field_diag<float>(g->dim, uc, (const float *)g->p, (const float *)g->div, g->n, g->acc, g->s));
+  } else {
+    const double *uc[3] = {(const double *)g->u[0], (const double *)g->u[1], (const double *)g->u[2]};
+    IB_CUDA(launch_field_diag<double>(g->dim, uc, (const double *)g->p, (const double *)g->div, g->n, g->acc,
+                                      g->s));
+  }
+  const double *Xc[3] = {g->X[0], g->X[1], g->X[2]};
+  IB_CUDA(launch_marker_diag(g->dim, Xc, g->nm, g->edges, g->ekap, g->erest, g->ne, g->tris, g->nt, g->desc.H,
+                             g->acc, g->s));
+  double acc[8];
+  IB_CUDA(cudaMemcpyAsync(acc, g->acc, sizeof(acc), cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  double vol = 1.0;
+  for (int a = 0; a < g->dim; ++a) vol *= g->h[a];
+  out->div_l2 = sqrt(vol * acc[0]);
+  out->div_max = acc[1];
+  out->kinetic = 0.5 * g->desc.rho * vol * acc[2];
+  out->volume = acc[3];
+  out->elastic = acc[4];
+  out->step = g->step;
+  if ((rc = leave(g))) return rc;
+  if (acc[5] != 0.0 || !isfinite(acc[0]) || !isfinite(acc[2]) || !isfinite(acc[3]))
+    return fail(IB_ERR_NONFINITE, "%g non-finite values in the state", acc[5]);
+  return IB_OK;
+}
+
+int ib_cyclic_solve_lines(int precision, int dim, const int n[3], int axis, double r, const void *in, void *out,
+                          void *stream) {
+  if (!n || !in || !out) return fail(IB_ERR_ARG, "null argument");
+  if ((dim != 2 && dim != 3) || axis < 0 || axis >= dim) return fail(IB_ERR_ARG, "dim/axis");
+  if (precision != IB_FP32 && precision != IB_FP64) return fail(IB_ERR_ARG, "precision");
+  if (!(r >= 0)) return fail(IB_ERR_ARG, "r must be >= 0");
+  for (int a = 0; a < dim; ++a)
+    if (!valid_n(n[a])) return fail(IB_ERR_ARG, "n[%d] = %d outside [8, 512]", a, n[a]);
+  cudaStream_t s = (cudaStream_t)stream;
+  DevCoef *c;
+  int rc = cached_coef(n[axis], r, s, &c);
+  if (rc) return rc;
+  if (precision == IB_FP32) {
+    SweepArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    a.f[0] = (float *)out;
+    a.fin[0] = (const float *)in;
+    for (int q = 0; q < 3; ++q) a.n[q] = q < dim ? n[q] : 1;
+    a.dim = dim;
+    a.co = c->f;
+    IB_CUDA(launch_sweep<float>(axis, PRO_LOAD, EPI_STORE, 1, a, s));
+  } else {
+    SweepArgs<double> a;
+    memset(&a, 0, sizeof(a));
+    a.f[0] = (double *)out;
+    a.fin[0] = (const double *)in;
+    for (int q = 0; q < 3; ++q) a.n[q] = q < dim ? n[q] : 1;
+    a.dim = dim;
+    a.co = c->d;
+    IB_CUDA(launch_sweep<double>(axis, PRO_LOAD, EPI_STORE, 1, a, s));
+  }
+  return IB_OK;
+}
+
+int ib_split_solve(int precision, int dim, const int n[3], const double r[3], const void *f, void *psi,
+                   void *stream) {
+  if (!r) return fail(IB_ERR_ARG, "null r");
+  for (int a = 0; a < (dim == 3 ? 3 : 2); ++a) {
+    int rc = ib_cyclic_solve_lines(precision, dim, n, a, r[a], a == 0 ? f : psi, psi, stream);
+    if (rc) return rc;
+  }
+  return IB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Line-solve kernels instantiated for double fields.
+#include "ib_linesolve.cuh"
+
+namespace ibg {
+template <>
+cudaError_t launch_sweep<double>(int axis, int pro, int epi, int nfields, const SweepArgs<double> &a, cudaStream_t s) {
+  return launch_sweep_impl<double>(axis, pro, epi, nfields, a, s);
+}
+}  // namespace ibg
