@@ -167,6 +167,31 @@ int ib_cyclic_solve_lines(int precision, int dim, const int n[3], int axis, doub
 int ib_split_solve(int precision, int dim, const int n[3], const double r[3], const void *f,
                    void *psi, void *stream);
 
+/* Allocation-free variant of ib_split_solve.  The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory: processes whose
+ * device memory belongs to another allocator (a framework's caching
+ * allocator, a budget fixed at start-up) and latency-critical loops that must
+ * not call cudaMalloc because it synchronises the device.  ib_split_solve
+ * allocates a small table of powers lam^k per (n, r) on first use; this
+ * variant keeps those tables in one fixed array inside the library (file-scope
+ * __device__ storage of about 25 KB that every GPU loading the library holds
+ * until the process exits) and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Same arguments, layout, result and stream ordering as
+ * ib_split_solve.
+ *   - Line lengths are limited to IB_NOALLOC_MAX_N (= 512); a larger n[a]
+ *     returns IB_ERR_ARG with a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call rewrites the shared array before its solves read it, so no
+ *     state carries over between calls, but calls whose work overlaps on the
+ *     GPU (different streams, or different host threads) race on the array:
+ *     order them on one stream.
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+#define IB_NOALLOC_MAX_N 512
+int ib_split_solve_noalloc(int precision, int dim, const int n[3], const double r[3], const void *f,
+                           void *psi, void *stream);
+
 /* Run n_steps steps with every kernel launched on its own and timed by CUDA
  * events on the grid's stream; kernel_ms[i] receives the total milliseconds
  * of kernel slot i (at most max_kernels slots, *n_kernels gets the count) and

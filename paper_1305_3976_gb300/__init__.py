@@ -25,7 +25,8 @@ FIELD_BITS = ("u", "v", "w", "p", "psi", "div")
 
 EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_read_fields", "ib_read_markers",
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
-           "ib_cyclic_solve_lines", "ib_split_solve", "ib_profile_step", "ib_kernel_name")
+           "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
+           "ib_kernel_name")
 
 
 class ib_grid_desc(C.Structure):
@@ -69,6 +70,7 @@ def lib():
         L.ib_last_error.restype = C.c_char_p
         L.ib_cyclic_solve_lines.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_double, vp, vp, vp]
         L.ib_split_solve.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp, vp, vp, vp]
+        L.ib_split_solve_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp, vp, vp, vp]
         L.ib_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
@@ -203,6 +205,16 @@ def ib_split_solve(precision, dim, n, r, f, psi, stream="current"):
     ra = (C.c_double * 3)(*(list(r) + [0.0] * (3 - len(r))))
     s = _current_stream() if stream == "current" else stream
     _check(lib().ib_split_solve(precision, dim, na, ra, _ptr(f)[0], _ptr(psi)[0], C.c_void_p(s)), "ib_split_solve")
+
+
+def ib_split_solve_noalloc(precision, dim, n, r, f, psi, stream="current"):
+    """ib_split_solve without any device allocation (fixed scratch inside the
+    library, lines up to IB_NOALLOC_MAX_N = 512)."""
+    na = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    ra = (C.c_double * 3)(*(list(r) + [0.0] * (3 - len(r))))
+    s = _current_stream() if stream == "current" else stream
+    _check(lib().ib_split_solve_noalloc(precision, dim, na, ra, _ptr(f)[0], _ptr(psi)[0], C.c_void_p(s)),
+           "ib_split_solve_noalloc")
 
 
 def ib_profile_step(g, n_steps):

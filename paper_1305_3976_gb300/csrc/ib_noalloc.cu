@@ -1,0 +1,135 @@
+// ib_split_solve_noalloc: the direction-split line solve of ib_split_solve
+// for callers that cannot allocate device memory.
+//
+// Who needs it: a host process whose device memory is owned by someone else
+// (a framework's caching allocator, a fixed memory budget handed out at
+// start-up) or a latency-critical loop that must not call cudaMalloc because
+// it synchronises the whole device.  ib_split_solve allocates a small table of
+// powers lam^k per (n, r) the first time it sees them; this variant keeps that
+// table in a fixed array inside the library instead and allocates nothing.
+//
+// The scratch: one file-scope __device__ array of 2 x 3 x (IB_NOALLOC_MAX_N + 8)
+// doubles (about 25 KB).  Every GPU that loads the library holds it until the
+// process exits.  Host code cannot use the array's name as a device address,
+// so the first call on each device looks the address up with
+// cudaGetSymbolAddress while that device is current and caches it.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/ib_gb300.h"
+#include "ib_internal.cuh"
+
+using namespace ibg;
+
+namespace {
+
+constexpr int kMaxN = IB_NOALLOC_MAX_N;
+constexpr int kRow = kMaxN + 8;  // one table of lam^0 .. lam^n per axis
+constexpr int kMaxDevices = 64;
+
+// [0][axis][k]: FP64 table; [1][axis][...]: FP32 table stored in the first
+// half of the row's bytes.  Rewritten completely by every call.
+static __device__ __align__(256) double g_noalloc_pw[2][3][kRow];
+
+std::mutex g_mu;
+double *g_addr[kMaxDevices] = {};
+
+// lam^k for k = 0..n of every axis; blockIdx.x = axis.  lam^k by binary
+// powering in FP64, the FP32 table is the FP64 value rounded.
+__global__ void k_fill_powers(double *base, int n0, int n1, int n2, double l0, double l1, double l2) {
+  const int a = blockIdx.x;
+  const int n = a == 0 ? n0 : (a == 1 ? n1 : n2);
+  const double lam = a == 0 ? l0 : (a == 1 ? l1 : l2);
+  double *pd = base + (size_t)a * kRow;
+  float *pf = reinterpret_cast<float *>(base + (size_t)(3 + a) * kRow);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+    double p = 1.0, b = lam;
+    for (int e = k; e > 0; e >>= 1) {
+      if (e & 1) p *= b;
+      b *= b;
+    }
+    pd[k] = p;
+    pf[k] = (float)p;
+  }
+}
+
+}  // namespace
+
+// defined in ib_runtime.cu: records the message returned by ib_last_error()
+int ib_internal_fail(int code, const char *msg);
+
+extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], const double r[3], const void *f,
+                                      void *psi, void *stream) {
+  if (!n || !r || !f || !psi) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: null argument");
+  if (dim != 2 && dim != 3) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: dim must be 2 or 3");
+  if (precision != IB_FP32 && precision != IB_FP64)
+    return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: precision");
+  for (int a = 0; a < dim; ++a) {
+    if (n[a] > kMaxN) {
+      char buf[160];
+      snprintf(buf, sizeof(buf), "ib_split_solve_noalloc: n[%d] = %d exceeds the fixed scratch limit of %d", a, n[a],
+               kMaxN);
+      return ib_internal_fail(IB_ERR_ARG, buf);
+    }
+    if (n[a] < 8) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: n must be >= 8");
+    if (!(r[a] >= 0)) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: r must be >= 0");
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: device index");
+  double *base;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_pw);
+      if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+      g_addr[dev] = (double *)p;
+    }
+    base = g_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double lam[3] = {0, 0, 0}, inv_c[3] = {1, 1, 1}, inv_1m[3] = {1, 1, 1};
+  int nn[3] = {8, 8, 8};
+  for (int a = 0; a < dim; ++a) {
+    const double q = 1.0 + 2.0 * r[a] + sqrt(1.0 + 4.0 * r[a]);
+    lam[a] = 2.0 * r[a] / q;
+    inv_c[a] = 2.0 / q;
+    double p = 1.0;
+    for (int k = 0; k < n[a]; ++k) p *= lam[a];
+    inv_1m[a] = 1.0 / (1.0 - p);
+    nn[a] = n[a];
+  }
+  k_fill_powers<<<dim, 128, 0, s>>>(base, nn[0], nn[1], nn[2], lam[0], lam[1], lam[2]);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+  for (int a = 0; a < dim; ++a) {
+    if (precision == IB_FP32) {
+      SweepArgs<float> sa;
+      memset(&sa, 0, sizeof(sa));
+      sa.f[0] = (float *)psi;
+      sa.fin[0] = a == 0 ? (const float *)f : nullptr;
+      for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
+      sa.dim = dim;
+      sa.co = LineCoef<float>{reinterpret_cast<const float *>(base + (size_t)(3 + a) * kRow), (float)lam[a],
+                              (float)inv_c[a], (float)inv_1m[a]};
+      e = launch_sweep<float>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
+    } else {
+      SweepArgs<double> sa;
+      memset(&sa, 0, sizeof(sa));
+      sa.f[0] = (double *)psi;
+      sa.fin[0] = a == 0 ? (const double *)f : nullptr;
+      for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
+      sa.dim = dim;
+      sa.co = LineCoef<double>{base + (size_t)a * kRow, lam[a], inv_c[a], inv_1m[a]};
+      e = launch_sweep<double>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
+    }
+    if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return IB_OK;
+}

@@ -128,6 +128,9 @@ int cached_coef(int n, double r, cudaStream_t s, DevCoef **out) {
 
 const char *ib_kernel_name(int slot);
 
+// error recording for the other translation units of the library
+int ib_internal_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+
 struct ib_grid_s {
   ib_grid_desc desc;
   int dim = 0, prec = 0;
