@@ -6,6 +6,25 @@
 
 namespace ibg {
 
+// 4 contiguous elements at p (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0];
+  const double2 b = reinterpret_cast<const double2 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+
 // Coefficients of one constant-coefficient cyclic line operator
 //   A = (1 + 2r) I - r (S + S^{-1})      (S the cyclic shift, eq. TriDiagX)
 // written as the exact product A = c (I - lam S)(I - lam S^{-1}) with
@@ -53,12 +72,17 @@ struct RhsArgs {
 };
 
 struct MarkerArgs {
-  // markers, FP64 SoA
-  double *X[3];   // X^n (updated to X^{n+1} by the force kernel)
-  double *Xh[3];  // X^{n+1/2}
-  double *U[3];   // U^n
-  double *Uold[3];// U^{n-1}
-  double *G[3];   // nodal force at X^{n+1/2}
+  double *X[3];     // X^n, FP64 (advanced to X^{n+1} by the update kernel)
+  double *Xh[3];    // X^{n+1/2}, FP64
+  void *U[3];       // U^n, field precision
+  void *Uold[3];    // U^{n-1}, field precision
+  void *G[3];       // nodal force at X^{n+1/2}, field precision
+  // grid locations, slot 2a + o for axis a and MAC offset o (0: own axis,
+  // 1: half a cell): index of the first stencil node and the 4 node weights
+  int32_t *locI_b;  // [2d][nm] of X^n (interpolation)
+  void *locI_w;     // [2d][nm][4] field precision
+  int32_t *locS_b;  // [2d][nm] of X^{n+1/2} (spreading)
+  void *locS_w;
   const int64_t *row;   // CSR over markers: neighbours of marker a are
   const int32_t *col;   //   col[row[a] .. row[a+1]) with
   const double *kap;    //   spring constants kap[] and rest lengths rest[]
@@ -80,13 +104,18 @@ template <typename T>
 cudaError_t launch_divergence(int dim, const T *const u[3], T *div, const int n[3], const T inv_h[3],
                               cudaStream_t s);
 template <typename T>
+cudaError_t launch_locate(const MarkerArgs &m, cudaStream_t s);
+template <typename T>
 cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t s);
+template <typename T>
+cudaError_t launch_update(const MarkerArgs &m, cudaStream_t s);
+template <typename T>
 cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s);
 
-cudaError_t launch_markers_layout(double *aos, double *const X[3], int64_t nm, int dim, int to_soa,
-                                  cudaStream_t s);
+cudaError_t launch_markers_layout(double *aos, double *const X[3], const int32_t *perm, int64_t nm, int dim,
+                                  int to_soa, cudaStream_t s);
 
 struct DiagAccum {
   double div2, divmax, kin, vol, elastic, nonfinite;

@@ -1,166 +1,10 @@
-// Marker kernels (Steps 1a-2b), the explicit momentum right-hand side
-// (Steps 3a-3b), the divergence and the FP64 diagnostics, for sm_103a.
+// The explicit momentum right-hand side (Steps 3a-3b), the divergence and
+// the FP64 diagnostics, for sm_103a.
 #include <math.h>
 
 #include "ib_internal.cuh"
 
 namespace ibg {
-
-// ---------------------------------------------------------------------------
-// 1D kernel weights.  For a node offset o (0 on the component's own axis,
-// 1/2 elsewhere) put x = X/h - o, i0 = floor(x), f = x - i0; the four nodes
-// i0-1 .. i0+2 sit at r = -1-f, -f, 1-f, 2-f.  Both branches of the 4-point
-// kernel of eq. (discretedelta) share q = sqrt(1 + 4f - 4f^2) on these four
-// nodes, which gives the weights (3-2f-q)/8, (3-2f+q)/8, (1+2f+q)/8,
-// (1+2f-q)/8 (they sum to 1).  The cosine kernel is (1 + cos(pi r / 2)) / 4.
-// Positions are FP64; the weights are computed in the field precision T.
-
-__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
-__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
-
-template <typename T>
-__device__ __forceinline__ long long delta_weights(double X, double inv_h, double off, int kernel, T (&w)[4]) {
-  const double x = X * inv_h - off;
-  const double fl = floor(x);
-  const T f = (T)(x - fl);
-  if (kernel == 0) {
-    const T q = sqrt(T(1) + T(4) * f * (T(1) - f));
-    const T a = T(3) - T(2) * f, b = T(1) + T(2) * f;
-    w[0] = (a - q) * T(0.125);
-    w[1] = (a + q) * T(0.125);
-    w[2] = (b + q) * T(0.125);
-    w[3] = (b - q) * T(0.125);
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = T(0.25) * (T(1) + cospi_t((T(j - 1) - f) * T(0.5)));
-  }
-  return (long long)fl - 1;
-}
-
-__device__ __forceinline__ int wrap_idx(long long i, int n) {
-  long long r = i % n;
-  return (int)(r < 0 ? r + n : r);
-}
-
-// Step 1a + Steps 1b-1c: one thread per (marker, component c).
-//   U_c = sum over the 4^d nodes of u_c(node) prod_a phi_a
-//   X^{n+1/2}_c = 1/2 ((X_c + dt V_c) + X_c),  V = 3/2 U^n - 1/2 U^{n-1}
-//   (V = U^0 at n = 0).  X^{n+1} is written by the force kernel.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
-                                                const T *const u2) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.nm * DIM) return;
-  const long long k = t / DIM;
-  const int c = (int)(t % DIM);
-  const T *uc = c == 0 ? u0 : (c == 1 ? u1 : u2);
-  const int nx = m.n[0], ny = m.n[1];
-  T w[3][4];
-  int idx[3][4];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const long long b = delta_weights<T>(m.X[a][k], m.inv_h[a], a == c ? 0.0 : 0.5, m.kernel, w[a]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) idx[a][j] = wrap_idx(b + j, m.n[a]);
-  }
-  T s = T(0);
-  if (DIM == 2) {
-#pragma unroll
-    for (int jy = 0; jy < 4; ++jy) {
-      const T *row = uc + (long long)idx[1][jy] * nx;
-#pragma unroll
-      for (int ix = 0; ix < 4; ++ix) s += __ldg(row + idx[0][ix]) * (w[0][ix] * w[1][jy]);
-    }
-  } else {
-#pragma unroll
-    for (int kz = 0; kz < 4; ++kz)
-#pragma unroll
-      for (int jy = 0; jy < 4; ++jy) {
-        const T *row = uc + ((long long)idx[2][kz] * ny + idx[1][jy]) * nx;
-        const T wyz = w[1][jy] * w[2][kz];
-#pragma unroll
-        for (int ix = 0; ix < 4; ++ix) s += __ldg(row + idx[0][ix]) * (w[0][ix] * wyz);
-      }
-  }
-  const double U = (double)s;
-  const double vel = m.first ? U : 1.5 * U - 0.5 * m.Uold[c][k];
-  const double Xc = m.X[c][k];
-  m.Xh[c][k] = 0.5 * ((Xc + m.dt * vel) + Xc);
-  m.U[c][k] = U;
-}
-
-// Step 2a over the force connections at X^{n+1/2} (CSR by marker), then the
-// marker update X^{n+1} = X^n + dt V of Step 1b.  One thread per (marker, c).
-template <int DIM>
-__global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.nm * DIM) return;
-  const long long a = t / DIM;
-  const int c = (int)(t % DIM);
-  double xa[DIM];
-#pragma unroll
-  for (int q = 0; q < DIM; ++q) xa[q] = m.Xh[q][a];
-  double g = 0.0;
-  for (long long e = m.row[a]; e < m.row[a + 1]; ++e) {
-    const int b = m.col[e];
-    double d[DIM], len2 = 0.0;
-#pragma unroll
-    for (int q = 0; q < DIM; ++q) {
-      d[q] = m.Xh[q][b] - xa[q];
-      d[q] -= m.H * round(d[q] / m.H);  // nearest periodic image
-      len2 += d[q] * d[q];
-    }
-    double scale = m.kap[e];
-    const double L = m.rest[e];
-    if (L != 0.0) scale *= 1.0 - L / sqrt(len2);
-    g += scale * d[c];
-  }
-  m.G[c][a] = g;
-  const double U = m.U[c][a];
-  const double vel = m.first ? U : 1.5 * U - 0.5 * m.Uold[c][a];
-  m.X[c][a] = m.X[c][a] + m.dt * vel;
-  m.Uold[c][a] = U;
-}
-
-// Step 2b: f_c(node) += G_c prod_a phi_a / h^d with atomics.  One thread per
-// (marker, c); the 4 nodes along x of a row are contiguous.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.nm * DIM) return;
-  const long long k = t / DIM;
-  const int c = (int)(t % DIM);
-  T *fc = c == 0 ? f0 : (c == 1 ? f1 : f2);
-  const int nx = m.n[0], ny = m.n[1];
-  T w[3][4];
-  int idx[3][4];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const long long b = delta_weights<T>(m.Xh[a][k], m.inv_h[a], a == c ? 0.0 : 0.5, m.kernel, w[a]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) idx[a][j] = wrap_idx(b + j, m.n[a]);
-  }
-  const T val = (T)(m.G[c][k] * m.inv_vol);
-  if (DIM == 2) {
-#pragma unroll
-    for (int jy = 0; jy < 4; ++jy) {
-      T *row = fc + (long long)idx[1][jy] * nx;
-      const T vy = val * w[1][jy];
-#pragma unroll
-      for (int ix = 0; ix < 4; ++ix) atomicAdd(row + idx[0][ix], vy * w[0][ix]);
-    }
-  } else {
-#pragma unroll
-    for (int kz = 0; kz < 4; ++kz)
-#pragma unroll
-      for (int jy = 0; jy < 4; ++jy) {
-        T *row = fc + ((long long)idx[2][kz] * ny + idx[1][jy]) * nx;
-        const T vyz = val * (w[1][jy] * w[2][kz]);
-#pragma unroll
-        for (int ix = 0; ix < 4; ++ix) atomicAdd(row + idx[0][ix], vyz * w[0][ix]);
-      }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Steps 3a-3b in increment form: R_c = u*_c - u^n_c
@@ -190,34 +34,172 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
       dp[2] = k + 1 == nz ? pl * (1 - nz) : pl;
       dm[2] = k == 0 ? pl * (nz - 1) : -pl;
     }
+    // every load first (the stores below may alias nothing the compiler can see)
+    T uc[DIM], up[DIM][DIM], um[DIM][DIM], ux[DIM][DIM];  // ux[c][a] = u_a at face + e_a - e_c
+    T f[DIM], nold[DIM], pm[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      const T *uc = a.u[c];
-      const T u0 = uc[o];
+      const T *u = a.u[c];
+      uc[c] = u[o];
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) {
+        up[c][ax] = u[o + dp[ax]];
+        um[c][ax] = u[o + dm[ax]];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) ux[c][ax] = ax == c ? T(0) : a.u[ax][o + dp[ax] + dm[c]];
+    const T p0 = a.first ? T(0) : a.p[o] + a.psi[o];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      f[c] = a.scr[c][o];
+      nold[c] = a.first ? T(0) : a.Nold[c][o];
+      pm[c] = a.first ? T(0) : a.p[o + dm[c]] + a.psi[o + dm[c]];
+    }
+    T R[DIM], Nn[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
       T lap = T(0), adv = T(0);
 #pragma unroll
       for (int ax = 0; ax < DIM; ++ax) {
-        const T up = uc[o + dp[ax]], um = uc[o + dm[ax]];
-        lap += (up - T(2) * u0 + um) * a.inv_h2[ax];
+        lap += (up[c][ax] - T(2) * uc[c] + um[c][ax]) * a.inv_h2[ax];
         T Ap, Am;
         if (ax == c) {
-          Ap = T(0.5) * (u0 + up);
-          Am = T(0.5) * (um + u0);
+          Ap = T(0.5) * (uc[c] + up[c][ax]);
+          Am = T(0.5) * (um[c][ax] + uc[c]);
         } else {
-          const T *ua = a.u[ax];
-          Ap = T(0.5) * (ua[o + dp[ax]] + ua[o + dp[ax] + dm[c]]);
-          Am = T(0.5) * (ua[o] + ua[o + dm[c]]);
+          Ap = T(0.5) * (up[ax][ax] + ux[c][ax]);   // u_a at +e_a and at +e_a - e_c
+          Am = T(0.5) * (uc[ax] + um[ax][c]);       // u_a at the face and at -e_c
         }
-        adv += T(0.5) * (Ap * up - Am * um) * a.inv_h[ax];
+        adv += T(0.5) * (Ap * up[c][ax] - Am * um[c][ax]) * a.inv_h[ax];
       }
-      T gp = T(0);
-      if (!a.first) gp = ((a.p[o] + a.psi[o]) - (a.p[o + dm[c]] + a.psi[o + dm[c]])) * a.inv_h[c];
-      const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * a.Nold[c][o];
-      const T f = a.scr[c][o];
-      a.scr[c][o] = a.dt * ((a.mu * lap - gp + f) * a.inv_rho - Nh);
-      a.Nold[c][o] = adv;
+      const T gp = (p0 - pm[c]) * a.inv_h[c];
+      const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[c];
+      R[c] = a.dt * ((a.mu * lap - gp + f[c]) * a.inv_rho - Nh);
+      Nn[c] = adv;
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      a.scr[c][o] = R[c];
+      a.Nold[c][o] = Nn[c];
     }
   }
+}
+
+// 4 values of a row at x0 + shift .. x0 + 3 + shift (shift in {-1, 0, 1}),
+// periodic in x: one 128-bit load plus at most one single load
+template <typename T>
+__device__ __forceinline__ void get4(const T *f, int ro, int x0, int nx, int shift, T (&v)[4]) {
+  T c[4];
+  ld4(f + ro + x0, c);
+  if (shift == 0) {
+    v[0] = c[0]; v[1] = c[1]; v[2] = c[2]; v[3] = c[3];
+  } else if (shift < 0) {
+    v[0] = f[ro + (x0 == 0 ? nx - 1 : x0 - 1)];
+    v[1] = c[0]; v[2] = c[1]; v[3] = c[2];
+  } else {
+    v[0] = c[1]; v[1] = c[2]; v[2] = c[3];
+    v[3] = f[ro + (x0 + 4 == nx ? 0 : x0 + 4)];
+  }
+}
+
+// component C of the right-hand side at 4 consecutive x cells
+template <typename T, int DIM, int C>
+__device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int y, int z) {
+  const int nx = a.n[0], ny = a.n[1], nz = DIM == 3 ? a.n[2] : 1;
+  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+  const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+  auto R = [&](int yy, int zz) { return (zz * ny + yy) * nx; };
+  const int ro = R(y, z);
+  // u_C: centre and the 6 neighbours (dir 1/2 = +x/-x, 3/4 = +y/-y, 5/6 = +z/-z)
+  T S[7][4];
+  get4(a.u[C], ro, x0, nx, 0, S[0]);
+  get4(a.u[C], ro, x0, nx, 1, S[1]);
+  get4(a.u[C], ro, x0, nx, -1, S[2]);
+  get4(a.u[C], R(yp, z), x0, nx, 0, S[3]);
+  get4(a.u[C], R(ym, z), x0, nx, 0, S[4]);
+  if (DIM == 3) {
+    get4(a.u[C], R(y, zp), x0, nx, 0, S[5]);
+    get4(a.u[C], R(y, zm), x0, nx, 0, S[6]);
+  }
+  // for every other axis A: u_A at +e_A, at +e_A - e_C, at the face, at -e_C
+  T Up[DIM][4], Ux[DIM][4], U0[DIM][4], Um[DIM][4];
+#pragma unroll
+  for (int A = 0; A < DIM; ++A) {
+    if (A == C) continue;
+    const T *uA = a.u[A];
+    if (A == 0) get4(uA, ro, x0, nx, 1, Up[A]);
+    else if (A == 1) get4(uA, R(yp, z), x0, nx, 0, Up[A]);
+    else get4(uA, R(y, zp), x0, nx, 0, Up[A]);
+    int yy = y, zz = z, sh = 0;
+    if (A == 0) sh = 1; else if (A == 1) yy = yp; else zz = zp;
+    if (C == 0) sh -= 1; else if (C == 1) yy = ym; else zz = zm;
+    get4(uA, R(yy, zz), x0, nx, sh, Ux[A]);
+    get4(uA, ro, x0, nx, 0, U0[A]);
+    if (C == 0) get4(uA, ro, x0, nx, -1, Um[A]);
+    else if (C == 1) get4(uA, R(ym, z), x0, nx, 0, Um[A]);
+    else get4(uA, R(y, zm), x0, nx, 0, Um[A]);
+  }
+  T f[4], nold[4], P0[4], Pm[4];
+  ld4(a.scr[C] + ro + x0, f);
+  if (!a.first) {
+    T t0[4], t1[4];
+    ld4(a.Nold[C] + ro + x0, nold);
+    get4(a.p, ro, x0, nx, 0, t0);
+    get4(a.psi, ro, x0, nx, 0, t1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) P0[e] = t0[e] + t1[e];
+    const int rm = C == 0 ? ro : (C == 1 ? R(ym, z) : R(y, zm));
+    get4(a.p, rm, x0, nx, C == 0 ? -1 : 0, t0);
+    get4(a.psi, rm, x0, nx, C == 0 ? -1 : 0, t1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Pm[e] = t0[e] + t1[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nold[e] = P0[e] = Pm[e] = T(0);
+  }
+  T Rv[4], Nn[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const T u0 = S[0][e];
+    T lap = T(0), adv = T(0);
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const T up = S[1 + 2 * ax][e], um = S[2 + 2 * ax][e];
+      lap += (up - T(2) * u0 + um) * a.inv_h2[ax];
+      T Ap, Am;
+      if (ax == C) {
+        Ap = T(0.5) * (u0 + up);
+        Am = T(0.5) * (um + u0);
+      } else {
+        Ap = T(0.5) * (Up[ax][e] + Ux[ax][e]);
+        Am = T(0.5) * (U0[ax][e] + Um[ax][e]);
+      }
+      adv += T(0.5) * (Ap * up - Am * um) * a.inv_h[ax];
+    }
+    const T gp = (P0[e] - Pm[e]) * a.inv_h[C];
+    const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[e];
+    Rv[e] = a.dt * ((a.mu * lap - gp + f[e]) * a.inv_rho - Nh);
+    Nn[e] = adv;
+  }
+  st4(a.scr[C] + ro + x0, Rv);
+  st4(a.Nold[C] + ro + x0, Nn);
+}
+
+// The same right-hand side for n_x divisible by 4: a thread computes one
+// component at 4 consecutive x cells from 128-bit row loads, on a
+// (x/4, y, z * d + c) launch grid.  The arithmetic per cell is the one above.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_rhs4(const RhsArgs<T> a) {
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z / DIM, c = blockIdx.z - (blockIdx.z / DIM) * DIM;
+  if (x0 >= a.n[0] || y >= a.n[1]) return;
+  if (c == 0) rhs4_component<T, DIM, 0>(a, x0, y, z);
+  else if (c == 1) rhs4_component<T, DIM, 1>(a, x0, y, z);
+  else if (DIM == 3) rhs4_component<T, DIM, DIM == 3 ? 2 : 1>(a, x0, y, z);
 }
 
 template <typename T, int DIM>
@@ -328,25 +310,9 @@ __global__ void __launch_bounds__(256) k_marker_diag(int dim, const double *X0, 
   block_reduce_add<3>(v, acc, slot, -1);
 }
 
-// marker positions between the caller's [n][dim] layout and the SoA arrays
-__global__ void __launch_bounds__(256) k_markers_layout(double *aos, double *X0, double *X1, double *X2,
-                                                        long long nm, int dim, int to_soa) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nm * dim) return;
-  const long long k = t / dim;
-  const int c = (int)(t % dim);
-  double *X = c == 0 ? X0 : (c == 1 ? X1 : X2);
-  if (to_soa) X[k] = aos[t];
-  else aos[t] = X[k];
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 
-static inline unsigned blocks_for(long long work, int threads) {
-  long long b = (work + threads - 1) / threads;
-  return (unsigned)(b < 1 ? 1 : b);
-}
 static inline unsigned grid_stride_blocks(long long work) {
   // enough CTAs for every SM of a GB300 several times over, then grid-stride
   long long b = (work + 255) / 256;
@@ -355,33 +321,15 @@ static inline unsigned grid_stride_blocks(long long work) {
 }
 
 template <typename T>
-cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t s) {
-  if (m.nm == 0) return cudaSuccess;
-  const unsigned g = blocks_for(m.nm * m.dim, 256);
-  if (m.dim == 2) k_interp<T, 2><<<g, 256, 0, s>>>(m, u[0], u[1], u[1]);
-  else k_interp<T, 3><<<g, 256, 0, s>>>(m, u[0], u[1], u[2]);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s) {
-  if (m.nm == 0) return cudaSuccess;
-  const unsigned g = blocks_for(m.nm * m.dim, 256);
-  if (m.dim == 2) k_force<2><<<g, 256, 0, s>>>(m);
-  else k_force<3><<<g, 256, 0, s>>>(m);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s) {
-  if (m.nm == 0) return cudaSuccess;
-  const unsigned g = blocks_for(m.nm * m.dim, 256);
-  if (m.dim == 2) k_spread<T, 2><<<g, 256, 0, s>>>(m, f[0], f[1], f[1]);
-  else k_spread<T, 3><<<g, 256, 0, s>>>(m, f[0], f[1], f[2]);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s) {
+  if (sizeof(T) == 4 && (a.n[0] & 3) == 0) {  // FP64 keeps the scalar kernel (register pressure)
+    const dim3 blk(32, 8);
+    const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)((a.n[1] + 7) / 8),
+                    (unsigned)((dim == 3 ? a.n[2] : 1) * dim));
+    if (dim == 2) k_rhs4<T, 2><<<grid, blk, 0, s>>>(a);
+    else k_rhs4<T, 3><<<grid, blk, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   const long long cells = (long long)a.n[0] * a.n[1] * (dim == 3 ? a.n[2] : 1);
   const unsigned g = grid_stride_blocks(cells);
   if (dim == 2) k_rhs<T, 2><<<g, 256, 0, s>>>(a);
@@ -420,17 +368,6 @@ cudaError_t launch_marker_diag(int dim, const double *const X[3], int64_t nm, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_markers_layout(double *aos, double *const X[3], int64_t nm, int dim, int to_soa,
-                                  cudaStream_t s) {
-  if (nm == 0) return cudaSuccess;
-  k_markers_layout<<<blocks_for(nm * dim, 256), 256, 0, s>>>(aos, X[0], X[1], X[2], nm, dim, to_soa);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_interp<float>(const MarkerArgs &, const float *const[3], cudaStream_t);
-template cudaError_t launch_interp<double>(const MarkerArgs &, const double *const[3], cudaStream_t);
-template cudaError_t launch_spread<float>(const MarkerArgs &, float *const[3], cudaStream_t);
-template cudaError_t launch_spread<double>(const MarkerArgs &, double *const[3], cudaStream_t);
 template cudaError_t launch_rhs<float>(int, const RhsArgs<float> &, cudaStream_t);
 template cudaError_t launch_rhs<double>(int, const RhsArgs<double> &, cudaStream_t);
 template cudaError_t launch_divergence<float>(int, const float *const[3], float *, const int[3], const float[3],

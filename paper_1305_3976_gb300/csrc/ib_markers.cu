@@ -1,0 +1,372 @@
+// Marker kernels of one IB-GM step for sm_103a: interpolation (Step 1a), the
+// AB2 marker update and half position (Steps 1b-1c), the force connections
+// (Step 2a) and spreading (Step 2b).
+//
+// Positions are FP64.  Everything that needs FP64 arithmetic on positions
+// (the AB2 update and locating a marker on the grid) runs with one thread per
+// marker, where every lane does useful work: on GB300 a warp instruction on
+// the FP64 pipe costs the same whether 1 or 32 lanes are active.  The stencil
+// kernels (interpolation, spreading) then work in the field precision only,
+// from a stored location: for every axis a and MAC offset o (0 on the
+// component's own axis, 1/2 on the others) the index of the first of the 4
+// stencil nodes and their 4 weights.
+#include <math.h>
+
+#include "ib_internal.cuh"
+
+namespace ibg {
+
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+
+// periodic index in [0, n); one compare in the common case of an index
+// within one period of the box
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// Locations of one coordinate for both MAC offsets from a single FP64
+// product: x = X/h, i0 = floor(x), f0 = x - i0; for the half-cell offset the
+// fraction is f0 - 1/2 (same cell) or f0 + 1/2 (previous cell).
+template <typename T>
+__device__ __forceinline__ void locate2(double X, double inv_h, int &b0, T &f0, int &b1, T &f1) {
+  const double x = X * inv_h;
+  const double fl = floor(x);
+  f0 = (T)(x - fl);
+  b0 = (int)fl - 1;
+  if (f0 >= T(0.5)) {
+    f1 = f0 - T(0.5);
+    b1 = b0;
+  } else {
+    f1 = f0 + T(0.5);
+    b1 = b0 - 1;
+  }
+}
+
+// Weights of the 4 stencil nodes, at r = -1-f, -f, 1-f, 2-f.  Both branches
+// of the 4-point kernel of eq. (discretedelta) share q = sqrt(1 + 4f - 4f^2)
+// on these nodes: (3-2f-q)/8, (3-2f+q)/8, (1+2f+q)/8, (1+2f-q)/8 (sum 1).
+// The cosine kernel is (1 + cos(pi r / 2)) / 4.
+template <typename T>
+__device__ __forceinline__ void weights(T f, int kernel, T (&w)[4]) {
+  if (kernel == 0) {
+    const T q = sqrt(T(1) + T(4) * f * (T(1) - f));
+    const T a = T(3) - T(2) * f, b = T(1) + T(2) * f;
+    w[0] = (a - q) * T(0.125);
+    w[1] = (a + q) * T(0.125);
+    w[2] = (b + q) * T(0.125);
+    w[3] = (b - q) * T(0.125);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = T(0.25) * (T(1) + cospi_t((T(j - 1) - f) * T(0.5)));
+  }
+}
+
+// Location of coordinate X on axis a for both MAC offsets: first stencil
+// node b[2a + o] and the 4 weights w[2a + o][0..3] (stored as 4 consecutive
+// values of the field precision).
+template <typename T>
+__device__ __forceinline__ void store_location(const MarkerArgs &m, double X, int a, long long k, int32_t *lb,
+                                               T *lw) {
+  int b0, b1;
+  T f0, f1, w[4];
+  locate2<T>(X, m.inv_h[a], b0, f0, b1, f1);
+  const long long s0 = (2 * a) * m.nm + k, s1 = (2 * a + 1) * m.nm + k;
+  lb[s0] = b0;
+  lb[s1] = b1;
+  weights<T>(f0, m.kernel, w);
+  st4(lw + 4 * s0, w);
+  weights<T>(f1, m.kernel, w);
+  st4(lw + 4 * s1, w);
+}
+
+// Locations of every marker at its positions Xs (one thread per marker).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_locate(const MarkerArgs m, double *const X0, double *const X1,
+                                                double *const X2, int32_t *lb, T *lw) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.nm) return;
+  const double *Xs[3] = {X0, X1, X2};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) store_location<T>(m, Xs[a][k], a, k, lb, lw);
+}
+
+// Steps 1b-1c after interpolation, one thread per marker:
+//   V = 3/2 U^n - 1/2 U^{n-1} (U^0 at n = 0), X^{n+1} = X^n + dt V,
+//   X^{n+1/2} = (X^{n+1} + X^n) / 2, U^{n-1} <- U^n,
+// and the grid locations of X^{n+1/2} (spreading, this step) and of X^{n+1}
+// (interpolation, next step).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned k = t / DIM;
+  const int c = (int)(t - k * DIM);
+  if (k >= (unsigned)m.nm) return;
+  const unsigned nm = (unsigned)m.nm;
+  const T Ut = ((const T *)m.U[c])[k];
+  const double U = (double)Ut;
+  const double vel = m.first ? U : 1.5 * U - 0.5 * (double)((const T *)m.Uold[c])[k];
+  const double Xc = m.X[c][k];
+  const double Xn = Xc + m.dt * vel;
+  const double Xh = 0.5 * (Xn + Xc);
+  m.Xh[c][k] = Xh;
+  m.X[c][k] = Xn;
+  ((T *)m.Uold[c])[k] = Ut;
+  (void)nm;
+  store_location<T>(m, Xh, c, k, m.locS_b, (T *)m.locS_w);
+  store_location<T>(m, Xn, c, k, m.locI_b, (T *)m.locI_w);
+}
+
+// Lane groups for the 4^d-node stencils: one group of ROWS lanes per
+// (marker, component c) (16 in 3D, 4 in 2D); lane r owns the stencil row
+// (y, z) = (r & 3, r >> 2) and its 4 nodes along x.  Every lane reads the
+// stored locations and weights it needs.
+template <typename T, int DIM>
+struct StencilLanes {
+  static constexpr int ROWS = DIM == 3 ? 16 : 4;
+  unsigned k;  // marker
+  int c, row, jy, kz;
+  bool valid;
+  T wx[4], wrow;  // x weights; product of this row's y (and z) weights
+  int bx, yrow, zrow;
+  __device__ __forceinline__ StencilLanes(const MarkerArgs &m, const int32_t *lb, const T *lw) {
+    // 32-bit index arithmetic: marker count * d * ROWS < 2^31 (checked on the host)
+    const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned pair = gt / ROWS;
+    row = (int)(gt & (ROWS - 1));
+    k = pair / DIM;
+    c = (int)(pair - k * DIM);
+    valid = k < (unsigned)m.nm;
+    jy = row & 3;
+    kz = DIM == 3 ? row >> 2 : 0;
+    bx = yrow = zrow = 0;
+    wrow = T(0);
+    if (!valid) return;
+    const unsigned nm = (unsigned)m.nm;
+    unsigned s = 2 * 0 + (c == 0 ? 0 : 1);
+    bx = wrap_idx(lb[s * nm + k], m.n[0]);
+    ld4(lw + 4 * (s * nm + k), wx);
+    s = 2 * 1 + (c == 1 ? 0 : 1);
+    yrow = wrap_idx(lb[s * nm + k] + jy, m.n[1]);
+    wrow = lw[4 * (s * nm + k) + jy];
+    if (DIM == 3) {
+      s = 2 * 2 + (c == 2 ? 0 : 1);
+      zrow = wrap_idx(lb[s * nm + k] + kz, m.n[2]);
+      wrow *= lw[4 * (s * nm + k) + kz];
+    }
+  }
+  __device__ __forceinline__ long long row_offset(const MarkerArgs &m) const {
+    return ((long long)zrow * m.n[1] + yrow) * m.n[0];
+  }
+};
+
+// 4 consecutive values r[xs .. xs+3] of a row, periodic in x; two aligned
+// 128-bit loads when the 8-float block around xs lies inside the row
+__device__ __forceinline__ void row4(const float *r, int xs, int nx, float (&v)[4]) {
+  const int a0 = xs & ~3;
+  if ((nx & 3) == 0 && a0 + 8 <= nx) {
+    const float4 p = __ldg(reinterpret_cast<const float4 *>(r + a0));
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(r + a0 + 4));
+    const float t[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+    const int off = xs - a0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = off == 0 ? t[i] : off == 1 ? t[i + 1] : off == 2 ? t[i + 2] : t[i + 3];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __ldg(r + (xs + i < nx ? xs + i : xs + i - nx));
+  }
+}
+__device__ __forceinline__ void row4(const double *r, int xs, int nx, double (&v)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __ldg(r + (xs + i < nx ? xs + i : xs + i - nx));
+}
+
+// r[xs .. xs+3] += v, periodic in x; 128-bit vector atomics when the 8-float
+// block around xs lies inside the row (block lanes outside [xs, xs+3] add 0)
+__device__ __forceinline__ void row4_add(float *r, int xs, int nx, const float (&v)[4]) {
+  const int a0 = xs & ~3;
+  if ((nx & 3) == 0 && a0 + 8 <= nx) {
+    const int off = xs - a0;
+    float t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = i - off;
+      t[i] = q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : q == 3 ? v[3] : 0.0f;
+    }
+    atomicAdd(reinterpret_cast<float4 *>(r + a0), make_float4(t[0], t[1], t[2], t[3]));
+    if (off) atomicAdd(reinterpret_cast<float4 *>(r + a0 + 4), make_float4(t[4], t[5], t[6], t[7]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) atomicAdd(r + (xs + i < nx ? xs + i : xs + i - nx), v[i]);
+  }
+}
+__device__ __forceinline__ void row4_add(double *r, int xs, int nx, const double (&v)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) atomicAdd(r + (xs + i < nx ? xs + i : xs + i - nx), v[i]);
+}
+
+// Step 1a: U_c = sum over the 4^d nodes of u_c(node) prod_a phi_a, at X^n.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
+                                                const T *const u2) {
+  StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w);
+  T s = T(0);
+  if (L.valid) {
+    const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
+    T v[4];
+    row4(uc + L.row_offset(m), L.bx, m.n[0], v);
+    s = (v[0] * L.wx[0] + v[1] * L.wx[1] + v[2] * L.wx[2] + v[3] * L.wx[3]) * L.wrow;
+  }
+#pragma unroll
+  for (int off = StencilLanes<T, DIM>::ROWS / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (L.valid && L.row == 0) ((T *)m.U[L.c])[L.k] = s;
+}
+
+// Step 2a over the force connections at X^{n+1/2}: 8 lanes per marker share
+// its CSR row (lane j takes connections j, j+8, ...) and add their partial
+// forces with shuffles.  Differences X_b - X_a are taken in FP64 and reduced
+// to the nearest periodic image; the spring arithmetic runs in the field
+// precision.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
+  const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned a = gt >> 3;
+  const int lane8 = (int)(gt & 7);
+  const bool valid = a < (unsigned)m.nm;
+  T g[DIM];
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) g[q] = T(0);
+  if (valid) {
+    double xa[DIM];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) xa[q] = m.Xh[q][a];
+    const T H = (T)m.H, invH = (T)(1.0 / m.H);
+    const long long e1 = m.row[a + 1];
+    for (long long e = m.row[a] + lane8; e < e1; e += 8) {
+      const int b = m.col[e];
+      T d[DIM], len2 = T(0);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        d[q] = (T)(m.Xh[q][b] - xa[q]);
+        d[q] -= H * rint(d[q] * invH);  // nearest periodic image
+        len2 += d[q] * d[q];
+      }
+      T scale = (T)m.kap[e];
+      const double L = m.rest[e];
+      if (L != 0.0) scale *= T(1) - (T)L / sqrt(len2);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) g[q] += scale * d[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < DIM; ++q)
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) g[q] += __shfl_xor_sync(0xffffffffu, g[q], off);
+  if (valid && lane8 < DIM) {
+    const T gv = lane8 == 0 ? g[0] : (lane8 == 1 ? g[1] : g[DIM - 1]);
+    ((T *)m.G[lane8])[a] = gv;
+  }
+}
+
+// Step 2b: f_c(node) += G_c prod_a phi_a / h^d at X^{n+1/2} with global
+// atomics, one lane group per (marker, c), 128-bit vector atomics per row
+// where the row segment allows.  Markers are numbered in Morton order of
+// their initial positions, so neighbouring groups update neighbouring nodes.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
+  StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w);
+  if (!L.valid) return;
+  T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
+  const T val = ((const T *)m.G[L.c])[L.k] * (T)m.inv_vol * L.wrow;
+  T v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = val * L.wx[i];
+  row4_add(fc + L.row_offset(m), L.bx, m.n[0], v);
+}
+
+// marker positions between the caller's [n][dim] layout and the SoA arrays
+// (internal marker k is the caller's marker perm[k])
+__global__ void __launch_bounds__(256) k_markers_layout(double *aos, double *X0, double *X1, double *X2,
+                                                        const int32_t *perm, long long nm, int dim, int to_soa) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nm * dim) return;
+  const long long k = t / dim;
+  const int c = (int)(t % dim);
+  double *X = c == 0 ? X0 : (c == 1 ? X1 : X2);
+  const long long o = (long long)perm[k] * dim + c;
+  if (to_soa) X[k] = aos[o];
+  else aos[o] = X[k];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+static inline unsigned nblocks(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+cudaError_t launch_locate(const MarkerArgs &m, cudaStream_t s) {
+  if (m.nm == 0) return cudaSuccess;
+  if (m.dim == 2) k_locate<T, 2><<<nblocks(m.nm, 256), 256, 0, s>>>(m, m.X[0], m.X[1], m.X[1], m.locI_b, (T *)m.locI_w);
+  else k_locate<T, 3><<<nblocks(m.nm, 256), 256, 0, s>>>(m, m.X[0], m.X[1], m.X[2], m.locI_b, (T *)m.locI_w);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t s) {
+  if (m.nm == 0) return cudaSuccess;
+  const unsigned g = nblocks(m.nm * m.dim * (m.dim == 3 ? 16 : 4), 256);
+  if (m.dim == 2) k_interp<T, 2><<<g, 256, 0, s>>>(m, u[0], u[1], u[1]);
+  else k_interp<T, 3><<<g, 256, 0, s>>>(m, u[0], u[1], u[2]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const MarkerArgs &m, cudaStream_t s) {
+  if (m.nm == 0) return cudaSuccess;
+  if (m.dim == 2) k_update<T, 2><<<nblocks(m.nm * 2, 256), 256, 0, s>>>(m);
+  else k_update<T, 3><<<nblocks(m.nm * 3, 256), 256, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s) {
+  if (m.nm == 0) return cudaSuccess;
+  const unsigned g = nblocks(m.nm * 8, 256);
+  if (m.dim == 2) k_force<T, 2><<<g, 256, 0, s>>>(m);
+  else k_force<T, 3><<<g, 256, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s) {
+  if (m.nm == 0) return cudaSuccess;
+  const unsigned g = nblocks(m.nm * m.dim * (m.dim == 3 ? 16 : 4), 256);
+  if (m.dim == 2) k_spread<T, 2><<<g, 256, 0, s>>>(m, f[0], f[1], f[1]);
+  else k_spread<T, 3><<<g, 256, 0, s>>>(m, f[0], f[1], f[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_markers_layout(double *aos, double *const X[3], const int32_t *perm, int64_t nm, int dim,
+                                  int to_soa, cudaStream_t s) {
+  if (nm == 0) return cudaSuccess;
+  k_markers_layout<<<nblocks(nm * dim, 256), 256, 0, s>>>(aos, X[0], X[1], X[2], perm, nm, dim, to_soa);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_locate<float>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_locate<double>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_interp<float>(const MarkerArgs &, const float *const[3], cudaStream_t);
+template cudaError_t launch_interp<double>(const MarkerArgs &, const double *const[3], cudaStream_t);
+template cudaError_t launch_update<float>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_update<double>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_force<float>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_force<double>(const MarkerArgs &, cudaStream_t);
+template cudaError_t launch_spread<float>(const MarkerArgs &, float *const[3], cudaStream_t);
+template cudaError_t launch_spread<double>(const MarkerArgs &, double *const[3], cudaStream_t);
+
+}  // namespace ibg

@@ -18,6 +18,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -151,15 +152,20 @@ struct ib_grid_s {
   int nfibers = 0;
   bool markers_uploaded = false;
   void *mk = nullptr;           // one allocation for all marker data
-  double *X[3] = {}, *Xh[3] = {}, *U[3] = {}, *Uold[3] = {}, *G[3] = {};
+  double *X[3] = {}, *Xh[3] = {};
+  void *U[3] = {}, *Uold[3] = {}, *G[3] = {};  // field precision
+  int32_t *locI_b = nullptr, *locS_b = nullptr;  // [2d][nm] grid locations (see MarkerArgs)
+  void *locI_w = nullptr, *locS_w = nullptr;      // [2d][nm][4] their weights
   int64_t *row = nullptr;
   int32_t *col = nullptr, *edges = nullptr, *tris = nullptr;
   double *kap = nullptr, *rest = nullptr, *ekap = nullptr, *erest = nullptr;
   double *acc = nullptr;        // diagnostics accumulators (device)
   double *stage = nullptr;      // [nm][dim] staging buffer for marker I/O
+  int32_t *perm = nullptr;      // internal marker k is the caller's marker perm[k]
 
   int64_t step = 0;
   bool div_valid = false;
+  bool loc_valid = false;       // locI holds the grid locations of the current X
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -168,17 +174,8 @@ struct ib_grid_s {
 
 namespace {
 
-template <typename T>
-int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+MarkerArgs marker_args(ib_grid_s *g, bool first) {
   const int d = g->dim;
-  int order[3];
-  for (int i = 0; i < d; ++i) order[i] = (i + phase) % d;
-  auto mark = [&](int slot) -> int {
-    if (ev) IB_CUDA(cudaEventRecord(ev[slot], g->s));
-    return IB_OK;
-  };
-  int rc;
-  // markers
   MarkerArgs m;
   memset(&m, 0, sizeof(m));
   for (int a = 0; a < 3; ++a) {
@@ -190,6 +187,10 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     m.inv_h[a] = 1.0 / g->h[a];
     m.n[a] = g->n[a];
   }
+  m.locI_b = g->locI_b;
+  m.locI_w = g->locI_w;
+  m.locS_b = g->locS_b;
+  m.locS_w = g->locS_w;
   m.row = g->row;
   m.col = g->col;
   m.kap = g->kap;
@@ -202,15 +203,31 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   m.dim = d;
   m.kernel = g->desc.kernel;
   m.first = first ? 1 : 0;
+  return m;
+}
+
+template <typename T>
+int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+  const int d = g->dim;
+  int order[3];
+  for (int i = 0; i < d; ++i) order[i] = (i + phase) % d;
+  auto mark = [&](int slot) -> int {
+    if (ev) IB_CUDA(cudaEventRecord(ev[slot], g->s));
+    return IB_OK;
+  };
+  int rc;
+  MarkerArgs m = marker_args(g, first);
   const T *uc[3] = {(const T *)g->u[0], (const T *)g->u[1], (const T *)g->u[2]};
   T *sc[3] = {(T *)g->scr[0], (T *)g->scr[1], (T *)g->scr[2]};
   if ((rc = mark(0))) return rc;
   IB_CUDA(launch_interp<T>(m, uc, g->s));
   if ((rc = mark(1))) return rc;
-  IB_CUDA(launch_force(m, g->s));
+  IB_CUDA(launch_update<T>(m, g->s));
   if ((rc = mark(2))) return rc;
-  IB_CUDA(launch_spread<T>(m, sc, g->s));
+  IB_CUDA(launch_force<T>(m, g->s));
   if ((rc = mark(3))) return rc;
+  IB_CUDA(launch_spread<T>(m, sc, g->s));
+  if ((rc = mark(4))) return rc;
   // Steps 3a-3b
   RhsArgs<T> ra;
   memset(&ra, 0, sizeof(ra));
@@ -229,7 +246,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   ra.dt = (T)g->desc.dt;
   ra.first = first ? 1 : 0;
   IB_CUDA(launch_rhs<T>(d, ra, g->s));
-  if ((rc = mark(4))) return rc;
+  if ((rc = mark(5))) return rc;
   // Steps 3c-3d (+ z): increment-form Douglas sweeps on the scratch fields
   SweepArgs<T> sa;
   memset(&sa, 0, sizeof(sa));
@@ -249,7 +266,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     const int ax = order[st];
     sa.co = coef_of<T>(g->coef[0][ax]);
     IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, st == d - 1 ? EPI_ADDU : EPI_STORE, d, sa, g->s));
-    if ((rc = mark(5 + st))) return rc;
+    if ((rc = mark(6 + st))) return rc;
   }
   // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
   // last sweeps
@@ -260,7 +277,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
     const int epi = st == d - 1 ? EPI_P : EPI_STORE;
     IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s));
-    if ((rc = mark(8 + st))) return rc;
+    if ((rc = mark(9 + st))) return rc;
   }
   return IB_OK;
 }
@@ -287,21 +304,50 @@ int ensure_div(ib_grid_s *g) {
 
 // Build the device marker arrays and the CSR neighbour lists (once, before the
 // first step).
+// Interleave the low 10 bits of up to three cell coordinates (Morton order).
+uint64_t morton_key(const unsigned q[3], int d) {
+  uint64_t key = 0;
+  for (int bit = 9; bit >= 0; --bit)
+    for (int a = d - 1; a >= 0; --a) key = (key << 1) | ((q[a] >> bit) & 1u);
+  return key;
+}
+
 int upload_markers(ib_grid_s *g) {
   if (g->markers_uploaded) return IB_OK;
   const int d = g->dim;
   const int64_t nm = g->nm, ne = g->ne, nt = g->nt;
+  // Internal marker order: Morton order of the initial positions (wrapped into
+  // the box), so that runs of consecutive markers are spatially compact.
+  // perm[k] = caller's index of internal marker k; inv is its inverse.
+  std::vector<uint64_t> key(nm);
+  for (int64_t k = 0; k < nm; ++k) {
+    unsigned q[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      double x = g->hX[k * d + a] / g->desc.H;
+      x -= floor(x);
+      int c = (int)(x * 1024.0);
+      q[a] = (unsigned)(c < 0 ? 0 : (c > 1023 ? 1023 : c));
+    }
+    key[k] = morton_key(q, d);
+  }
+  std::vector<int32_t> perm(nm), inv(nm);
+  for (int64_t k = 0; k < nm; ++k) perm[k] = (int32_t)k;
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+  for (int64_t k = 0; k < nm; ++k) inv[perm[k]] = (int32_t)k;
+  std::vector<int32_t> E(2 * ne), Tr(3 * nt);
+  for (int64_t e = 0; e < 2 * ne; ++e) E[e] = inv[g->hE[e]];
+  for (int64_t t = 0; t < 3 * nt; ++t) Tr[t] = inv[g->hT[t]];
   std::vector<int64_t> row(nm + 1, 0);
   for (int64_t e = 0; e < ne; ++e) {
-    row[g->hE[2 * e] + 1]++;
-    row[g->hE[2 * e + 1] + 1]++;
+    row[E[2 * e] + 1]++;
+    row[E[2 * e + 1] + 1]++;
   }
   for (int64_t a = 0; a < nm; ++a) row[a + 1] += row[a];
   std::vector<int32_t> col(2 * ne);
   std::vector<double> kap(2 * ne), rest(2 * ne);
   std::vector<int64_t> fill(row.begin(), row.end() - 1);
   for (int64_t e = 0; e < ne; ++e) {
-    const int32_t a = g->hE[2 * e], b = g->hE[2 * e + 1];
+    const int32_t a = E[2 * e], b = E[2 * e + 1];
     int64_t pa = fill[a]++, pb = fill[b]++;
     col[pa] = b;
     col[pb] = a;
@@ -310,15 +356,18 @@ int upload_markers(ib_grid_s *g) {
   }
   std::vector<double> soa(nm * d);
   for (int64_t k = 0; k < nm; ++k)
-    for (int a = 0; a < d; ++a) soa[a * nm + k] = g->hX[k * d + a];
-  // layout: 5 d nm doubles | row | col | kap | rest | edges | ekap | erest | tris | acc
+    for (int a = 0; a < d; ++a) soa[a * nm + k] = g->hX[(int64_t)perm[k] * d + a];
+  // layout: X, Xh (FP64) | U, Uold, G (field precision) | row | col | kap |
+  // rest | edges | ekap | erest | tris | acc | stage | perm | locations
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off += (bytes + 255) / 256 * 256;
     return o;
   };
-  const size_t o_m = take(sizeof(double) * 5 * d * (nm + 1));
+  const size_t es = g->esz;
+  const size_t o_m = take(sizeof(double) * 2 * d * (nm + 1));
+  const size_t o_u = take(es * 3 * d * (nm + 1));
   const size_t o_row = take(sizeof(int64_t) * (nm + 1));
   const size_t o_col = take(sizeof(int32_t) * (2 * ne + 1));
   const size_t o_kap = take(sizeof(double) * (2 * ne + 1));
@@ -329,17 +378,27 @@ int upload_markers(ib_grid_s *g) {
   const size_t o_t = take(sizeof(int32_t) * (3 * nt + 1));
   const size_t o_acc = take(sizeof(double) * 8);
   const size_t o_stage = take(sizeof(double) * (nm * d + 1));
+  const size_t o_perm = take(sizeof(int32_t) * (nm + 1));
+  const size_t o_lib = take(sizeof(int32_t) * 2 * d * (nm + 1));
+  const size_t o_lsb = take(sizeof(int32_t) * 2 * d * (nm + 1));
+  const size_t o_lif = take(es * 4 * 2 * d * (nm + 1));
+  const size_t o_lsf = take(es * 4 * 2 * d * (nm + 1));
   if (cudaMalloc(&g->mk, off) != cudaSuccess) return fail(IB_ERR_OOM, "marker allocation of %zu bytes failed", off);
   char *base = (char *)g->mk;
   double *md = (double *)(base + o_m);
+  char *mu = base + o_u;
   for (int a = 0; a < 3; ++a) {
     const int aa = a < d ? a : d - 1;
     g->X[a] = md + (0 * d + aa) * nm;
     g->Xh[a] = md + (1 * d + aa) * nm;
-    g->U[a] = md + (2 * d + aa) * nm;
-    g->Uold[a] = md + (3 * d + aa) * nm;
-    g->G[a] = md + (4 * d + aa) * nm;
+    g->U[a] = mu + es * (0 * d + aa) * nm;
+    g->Uold[a] = mu + es * (1 * d + aa) * nm;
+    g->G[a] = mu + es * (2 * d + aa) * nm;
   }
+  g->locI_b = (int32_t *)(base + o_lib);
+  g->locS_b = (int32_t *)(base + o_lsb);
+  g->locI_w = base + o_lif;
+  g->locS_w = base + o_lsf;
   g->row = (int64_t *)(base + o_row);
   g->col = (int32_t *)(base + o_col);
   g->kap = (double *)(base + o_kap);
@@ -350,6 +409,7 @@ int upload_markers(ib_grid_s *g) {
   g->tris = (int32_t *)(base + o_t);
   g->acc = (double *)(base + o_acc);
   g->stage = (double *)(base + o_stage);
+  g->perm = (int32_t *)(base + o_perm);
   IB_CUDA(cudaMemsetAsync(g->mk, 0, off, g->s));
   if (nm) IB_CUDA(cudaMemcpyAsync(g->X[0], soa.data(), sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
   IB_CUDA(cudaMemcpyAsync(g->row, row.data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, g->s));
@@ -357,11 +417,12 @@ int upload_markers(ib_grid_s *g) {
     IB_CUDA(cudaMemcpyAsync(g->col, col.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    IB_CUDA(cudaMemcpyAsync(g->edges, g->hE.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->edges, E.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->ekap, g->hK.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->erest, g->hR.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
   }
-  if (nt) IB_CUDA(cudaMemcpyAsync(g->tris, g->hT.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, g->s));
+  if (nt) IB_CUDA(cudaMemcpyAsync(g->tris, Tr.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, g->s));
+  if (nm) IB_CUDA(cudaMemcpyAsync(g->perm, perm.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, g->s));
   IB_CUDA(cudaStreamSynchronize(g->s));  // host vectors above go out of scope
   g->markers_uploaded = true;
   return IB_OK;
@@ -395,9 +456,18 @@ int get_graph(ib_grid_s *g, int phase) {
   return IB_OK;
 }
 
+int ensure_loc(ib_grid_s *g) {
+  if (g->loc_valid) return IB_OK;
+  const MarkerArgs m = marker_args(g, false);
+  IB_CUDA(g->prec == IB_FP32 ? launch_locate<float>(m, g->s) : launch_locate<double>(m, g->s));
+  g->loc_valid = true;
+  return IB_OK;
+}
+
 int prepare(ib_grid_s *g) {
   int rc = upload_markers(g);
   if (rc) return rc;
+  if ((rc = ensure_loc(g))) return rc;
   if ((rc = ensure_div(g))) return rc;
   // capture the step graph of every split-order phase up front so that no
   // instantiation happens between later steps
@@ -514,7 +584,7 @@ int ib_add_fiber(ib_grid_t g, const double *X0, int64_t n_markers, const int32_t
   if (n_markers < 0 || n_edges < 0 || n_tris < 0) return fail(IB_ERR_ARG, "negative count");
   if (n_markers > 0 && !X0) return fail(IB_ERR_ARG, "null X0");
   if (n_edges > 0 && (!edges || !kappa)) return fail(IB_ERR_ARG, "null edges or kappa");
-  if (g->nm + n_markers > (int64_t)0x7fffffff) return fail(IB_ERR_ARG, "too many markers");
+  if (g->nm + n_markers > ((int64_t)1 << 25)) return fail(IB_ERR_ARG, "more than 2^25 markers");
   const int d = g->dim;
   for (int64_t i = 0; i < n_markers * d; ++i)
     if (!isfinite(X0[i])) return fail(IB_ERR_NONFINITE, "non-finite marker position");
@@ -576,15 +646,15 @@ int ib_step(ib_grid_t g, int n_steps) {
 
 int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels, int *n_kernels) {
   if (!g || !kernel_ms || n_steps < 0) return fail(IB_ERR_ARG, "bad argument");
-  const int nslots = 11;  // 3 marker + rhs + 3 momentum + 3 psi + end mark
+  const int nslots = 12;  // marks 0..11 (see below) + one end mark
+  const int nk = 11;      // interp, update, force, spread, rhs, 3 momentum + 3 psi sweeps
   cudaEvent_t ev[nslots + 1];
   for (int i = 0; i <= nslots; ++i) IB_CUDA(cudaEventCreate(&ev[i]));
-  std::vector<double> tot(nslots, 0.0);
+  std::vector<double> tot(nk, 0.0);
   int rc = enter(g);
   if (!rc) rc = prepare(g);
   for (int i = 0; i < n_steps && !rc; ++i) {
     const int phase = g->desc.rotate_split ? (int)(g->step % g->dim) : 0;
-    // slots of kernels that do not run in this configuration keep equal events
     for (int k = 0; k <= nslots; ++k) cudaEventRecord(ev[k], g->s);
     rc = enqueue_step(g, g->step == 0, phase, ev);
     if (rc) break;
@@ -593,29 +663,27 @@ int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels,
       rc = fail(IB_ERR_CUDA, "profiling sync");
       break;
     }
-    // marks: 0 before interp, 1 after interp, 2 after force, 3 after spread,
-    // 4 after rhs, 5 + s after the s-th momentum sweep, 8 + s after the s-th
-    // psi sweep (s in split order); slots of a 2D step leave equal marks
+    // marks: 0 before interp, 1 after interp, 2 after update, 3 after force,
+    // 4 after spread, 5 after rhs, 6 + s after the s-th momentum sweep, 9 + s
+    // after the s-th psi sweep (s in split order)
     float ms;
-    const int last_m = 5 + g->dim - 1, last_p = 8 + g->dim - 1;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
       cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
       tot[k] += ms;
     }
+    const int last_m = 6 + g->dim - 1;
     for (int q = 0; q < g->dim; ++q) {
-      cudaEventElapsedTime(&ms, ev[4 + q], ev[5 + q]);
-      tot[4 + q] += ms;
+      cudaEventElapsedTime(&ms, ev[5 + q], ev[6 + q]);
+      tot[5 + q] += ms;
     }
     for (int q = 0; q < g->dim; ++q) {
-      cudaEventElapsedTime(&ms, q == 0 ? ev[last_m] : ev[7 + q], ev[8 + q]);
-      tot[7 + q] += ms;
+      cudaEventElapsedTime(&ms, q == 0 ? ev[last_m] : ev[8 + q], ev[9 + q]);
+      tot[8 + q] += ms;
     }
-    (void)last_p;
     g->step++;
   }
   for (int i = 0; i <= nslots; ++i) cudaEventDestroy(ev[i]);
   if (rc) return rc;
-  const int nk = 10;
   for (int k = 0; k < nk && k < max_kernels; ++k) kernel_ms[k] = (float)tot[k];
   if (n_kernels) *n_kernels = nk < max_kernels ? nk : max_kernels;
   return leave(g);
@@ -623,9 +691,10 @@ int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels,
 
 const char *ib_kernel_name(int slot) {
   // sweeps are numbered by their position in the step's split order
-  static const char *names[] = {"interp",      "force",       "spread",      "rhs",         "mom_sweep_1",
-                                "mom_sweep_2", "mom_sweep_3", "psi_sweep_1", "psi_sweep_2", "psi_sweep_3"};
-  return (slot >= 0 && slot < 10) ? names[slot] : "";
+  static const char *names[] = {"interp",      "update",      "force",       "spread",
+                                "rhs",         "mom_sweep_1", "mom_sweep_2", "mom_sweep_3",
+                                "psi_sweep_1", "psi_sweep_2", "psi_sweep_3"};
+  return (slot >= 0 && slot < 11) ? names[slot] : "";
 }
 
 int ib_read_fields(ib_grid_t g, unsigned field_mask, void *dst, size_t bytes, int dst_on_device) {
@@ -661,7 +730,7 @@ int ib_read_markers(ib_grid_t g, double *X, int64_t n, int dst_on_device) {
   if ((rc = upload_markers(g))) return rc;
   const int d = g->dim;
   // SoA on the device -> [n][dim] staging -> caller
-  IB_CUDA(launch_markers_layout(g->stage, g->X, n, d, 0, g->s));
+  IB_CUDA(launch_markers_layout(g->stage, g->X, g->perm, n, d, 0, g->s));
   IB_CUDA(cudaMemcpyAsync(X, g->stage, sizeof(double) * n * d,
                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->s));
   if (!dst_on_device) IB_CUDA(cudaStreamSynchronize(g->s));
@@ -678,7 +747,9 @@ int ib_set_markers(ib_grid_t g, const double *X, int64_t n, int src_on_device) {
   const int d = g->dim;
   IB_CUDA(cudaMemcpyAsync(g->stage, X, sizeof(double) * n * d,
                           src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
-  IB_CUDA(launch_markers_layout(g->stage, g->X, n, d, 1, g->s));
+  IB_CUDA(launch_markers_layout(g->stage, g->X, g->perm, n, d, 1, g->s));
+  g->loc_valid = false;
+  if ((rc = ensure_loc(g))) return rc;
   if (!src_on_device) IB_CUDA(cudaStreamSynchronize(g->s));
   return leave(g);
 }
