@@ -148,6 +148,24 @@ int ib_destroy_grid(ib_grid_t g);
 const char *ib_error_string(int code);
 const char *ib_last_error(void);
 
+/* Ensembles of independent grids (each with its own size, parameters and
+ * structures) advanced together: every step of the ensemble is one CUDA graph
+ * launch in which each member's kernels form an independent branch, so the
+ * members' kernels run concurrently on the GPU.  The paper runs one problem at
+ * a time; this batches many.
+ *   ib_create_ensemble: members are existing grids (the ensemble does not own
+ *     them) that all have the same dim, the same rotate_split and the same
+ *     step count; their structures must already be added.  stream: as in
+ *     ib_grid_desc.
+ *   ib_ensemble_step: advances every member by n_steps (Sec. 3.4), ordered
+ *     after earlier work on the members; afterwards the members can be read
+ *     or stepped on their own.
+ * Errors: IB_ERR_ARG, IB_ERR_STATE (mismatched members), IB_ERR_CUDA. */
+typedef struct ib_ensemble_s *ib_ensemble_t;
+int ib_create_ensemble(const ib_grid_t *members, int n_members, void *stream, ib_ensemble_t *out);
+int ib_ensemble_step(ib_ensemble_t e, int n_steps);
+int ib_destroy_ensemble(ib_ensemble_t e);
+
 /* Batched constant-coefficient cyclic tridiagonal solve along one axis
  * (Sec. 4.2, eq. TriDiagX): every line along `axis` of the n0 x n1 x n2 field
  * `in` is replaced by the solution x of

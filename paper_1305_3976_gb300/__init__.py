@@ -26,7 +26,7 @@ FIELD_BITS = ("u", "v", "w", "p", "psi", "div")
 EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_read_fields", "ib_read_markers",
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
-           "ib_kernel_name")
+           "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble")
 
 
 class ib_grid_desc(C.Structure):
@@ -72,6 +72,9 @@ def lib():
         L.ib_split_solve.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp, vp, vp, vp]
         L.ib_split_solve_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), dp, vp, vp, vp]
         L.ib_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+        L.ib_create_ensemble.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
+        L.ib_ensemble_step.argtypes = [vp, C.c_int]
+        L.ib_destroy_ensemble.argtypes = [vp]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
         for name in EXPORTS:
@@ -224,6 +227,22 @@ def ib_profile_step(g, n_steps):
     return {lib().ib_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
 
 
+def ib_create_ensemble(members, stream="current"):
+    arr = (C.c_void_p * len(members))(*[m.value if isinstance(m, C.c_void_p) else m for m in members])
+    h = C.c_void_p()
+    st = _current_stream() if stream == "current" else stream
+    _check(lib().ib_create_ensemble(arr, len(members), C.c_void_p(st), C.byref(h)), "ib_create_ensemble")
+    return h
+
+
+def ib_ensemble_step(e, n_steps=1):
+    _check(lib().ib_ensemble_step(e, int(n_steps)), "ib_ensemble_step")
+
+
+def ib_destroy_ensemble(e):
+    _check(lib().ib_destroy_ensemble(e), "ib_destroy_ensemble")
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 
@@ -292,6 +311,28 @@ class Grid:
     def close(self):
         if self.h:
             ib_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent Grids advanced together (one CUDA graph launch per step)."""
+
+    def __init__(self, grids, stream="current"):
+        self.grids = list(grids)
+        self.h = ib_create_ensemble([g.h for g in self.grids], stream)
+
+    def step(self, n=1):
+        ib_ensemble_step(self.h, n)
+
+    def close(self):
+        if self.h:
+            ib_destroy_ensemble(self.h)
             self.h = None
 
     def __del__(self):

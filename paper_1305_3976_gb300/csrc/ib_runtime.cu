@@ -833,3 +833,146 @@ int ib_split_solve(int precision, int dim, const int n[3], const double r[3], co
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ensembles
+
+struct ib_ensemble_s {
+  std::vector<ib_grid_s *> m;
+  cudaStream_t s = nullptr, user = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int dim = 0;
+};
+
+namespace {
+
+// one step of every member: fork from the ensemble stream into the members'
+// streams, one branch per member, then join back
+int ens_enqueue(ib_ensemble_s *e, bool first, int phase) {
+  IB_CUDA(cudaEventRecord(e->ev_fork, e->s));
+  for (size_t i = 0; i < e->m.size(); ++i) {
+    ib_grid_s *g = e->m[i];
+    IB_CUDA(cudaStreamWaitEvent(g->s, e->ev_fork, 0));
+    int rc = enqueue_step(g, first, phase, nullptr);
+    if (rc) return rc;
+    IB_CUDA(cudaEventRecord(e->ev_join[i], g->s));
+    IB_CUDA(cudaStreamWaitEvent(e->s, e->ev_join[i], 0));
+  }
+  return IB_OK;
+}
+
+int ens_graph(ib_ensemble_s *e, int phase) {
+  if (e->graph[phase]) return IB_OK;
+  cudaGraph_t graph;
+  IB_CUDA(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal));
+  int rc = ens_enqueue(e, false, phase);
+  cudaError_t err = cudaStreamEndCapture(e->s, &graph);
+  if (rc != IB_OK) {
+    if (err == cudaSuccess) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (err != cudaSuccess) return fail(IB_ERR_CUDA, "ensemble capture: %s", cudaGetErrorString(err));
+  err = cudaGraphInstantiate(&e->graph[phase], graph, 0);
+  cudaGraphDestroy(graph);
+  if (err != cudaSuccess) return fail(IB_ERR_CUDA, "ensemble instantiate: %s", cudaGetErrorString(err));
+  return IB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ib_destroy_ensemble(ib_ensemble_t e) {
+  if (!e) return IB_OK;
+  if (e->s) cudaStreamSynchronize(e->s);
+  for (int i = 0; i < 3; ++i)
+    if (e->graph[i]) cudaGraphExecDestroy(e->graph[i]);
+  for (cudaEvent_t ev : e->ev_join)
+    if (ev) cudaEventDestroy(ev);
+  if (e->ev_in) cudaEventDestroy(e->ev_in);
+  if (e->ev_out) cudaEventDestroy(e->ev_out);
+  if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+  if (e->s) cudaStreamDestroy(e->s);
+  delete e;
+  return IB_OK;
+}
+
+int ib_create_ensemble(const ib_grid_t *members, int n_members, void *stream, ib_ensemble_t *out) {
+  if (!members || !out || n_members < 1) return fail(IB_ERR_ARG, "need at least one member");
+  *out = nullptr;
+  const ib_grid_s *g0 = members[0];
+  if (!g0) return fail(IB_ERR_ARG, "null member");
+  for (int i = 0; i < n_members; ++i) {
+    const ib_grid_s *g = members[i];
+    if (!g) return fail(IB_ERR_ARG, "null member %d", i);
+    if (g->dim != g0->dim || g->desc.rotate_split != g0->desc.rotate_split || g->step != g0->step)
+      return fail(IB_ERR_STATE, "member %d differs in dim, rotate_split or step count", i);
+    for (int j = 0; j < i; ++j)
+      if (members[j] == g) return fail(IB_ERR_ARG, "member %d repeated", i);
+  }
+  ib_ensemble_s *e = new ib_ensemble_s();
+  e->dim = g0->dim;
+  e->user = (cudaStream_t)stream;
+  e->m.assign(members, members + n_members);
+  e->ev_join.assign(n_members, nullptr);
+  if (cudaStreamCreateWithFlags(&e->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    ib_destroy_ensemble(e);
+    return fail(IB_ERR_CUDA, "ensemble stream/event creation failed");
+  }
+  for (int i = 0; i < n_members; ++i)
+    if (cudaEventCreateWithFlags(&e->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      ib_destroy_ensemble(e);
+      return fail(IB_ERR_CUDA, "ensemble event creation failed");
+    }
+  for (ib_grid_s *g : e->m) {
+    int rc = enter(g);
+    if (!rc) rc = prepare(g);
+    if (!rc) rc = leave(g);
+    if (rc) {
+      ib_destroy_ensemble(e);
+      return rc;
+    }
+  }
+  *out = e;
+  return IB_OK;
+}
+
+int ib_ensemble_step(ib_ensemble_t e, int n_steps) {
+  if (!e) return fail(IB_ERR_ARG, "null ensemble");
+  if (n_steps < 0) return fail(IB_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return IB_OK;
+  for (ib_grid_s *g : e->m)
+    if (g->step != e->m[0]->step) return fail(IB_ERR_STATE, "members were stepped separately");
+  // order after the caller's stream and after earlier work on every member
+  IB_CUDA(cudaEventRecord(e->ev_in, e->user));
+  IB_CUDA(cudaStreamWaitEvent(e->s, e->ev_in, 0));
+  for (size_t i = 0; i < e->m.size(); ++i) {
+    IB_CUDA(cudaEventRecord(e->ev_join[i], e->m[i]->s));
+    IB_CUDA(cudaStreamWaitEvent(e->s, e->ev_join[i], 0));
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    const int64_t step = e->m[0]->step;
+    if (step == 0) {
+      int rc = ens_enqueue(e, true, 0);
+      if (rc) return rc;
+    } else {
+      const int phase = e->m[0]->desc.rotate_split ? (int)(step % e->dim) : 0;
+      int rc = ens_graph(e, phase);
+      if (rc) return rc;
+      IB_CUDA(cudaGraphLaunch(e->graph[phase], e->s));
+    }
+    for (ib_grid_s *g : e->m) g->step++;
+  }
+  // later work on the caller's stream and on every member comes after this
+  IB_CUDA(cudaEventRecord(e->ev_out, e->s));
+  IB_CUDA(cudaStreamWaitEvent(e->user, e->ev_out, 0));
+  for (ib_grid_s *g : e->m) IB_CUDA(cudaStreamWaitEvent(g->s, e->ev_out, 0));
+  return IB_OK;
+}
+
+}  // extern "C"

@@ -204,3 +204,122 @@ def thick_shell_2d(n=64, r1=0.2, r2=0.25, gamma=0.0625, mu=0.01, rho=1.0, dt=0.0
     return Scene(dim=2, n=(n, n), rho=rho, mu=mu, dt=dt, steps=steps, X=np.concatenate(Xs),
                  edges=np.concatenate(Es), kappa=np.concatenate(Ks), rest=np.concatenate(Rs),
                  kernel=kernel, name=f"2D thick shell {n}^2, {ns}x{nr} markers")
+
+
+def cylinder_3d(n=32, r1=5 / 28, r2=7 / 20, sigma_s=1.0, sigma_r=1.0, L=1.0, mu=0.01, rho=1.0, dt=None,
+                steps=100, kernel="peskin4") -> Scene:
+    """Cylindrical elastic shell of Sec. 6: X(s, r) = (r, 1/2 + r1 cos 2 pi s,
+    1/2 + r2 sin 2 pi s), N_s = 19N/4 circumferential points times N_r = 3N
+    axial points, each end joined to its periodic copy.  Circumferential
+    connections: spring sigma_s h_r / h_s, rest length 0; axial connections:
+    spring sigma_r h_s / h_r, rest length L h_r (quadrature weight h_s h_r per
+    point).  Default dt = 0.04/N."""
+    ns, nr = 19 * n // 4, 3 * n
+    hs, hr = 1.0 / ns, 1.0 / nr
+    s = np.arange(ns) * hs
+    r = np.arange(nr) * hr
+    S, Rr = np.meshgrid(s, r, indexing="ij")                 # point (k, l) -> k * nr + l
+    X = np.stack([Rr.ravel(), 0.5 + r1 * np.cos(2 * np.pi * S.ravel()),
+                  0.5 + r2 * np.sin(2 * np.pi * S.ravel())], axis=1)
+    idx = np.arange(ns * nr).reshape(ns, nr)
+    e_s = np.stack([idx.ravel(), np.roll(idx, -1, axis=0).ravel()], axis=1)
+    e_r = np.stack([idx.ravel(), np.roll(idx, -1, axis=1).ravel()], axis=1)
+    edges = np.concatenate([e_s, e_r]).astype(np.int32)
+    kappa = np.concatenate([np.full(len(e_s), sigma_s * hr / hs), np.full(len(e_r), sigma_r * hs / hr)])
+    rest = np.concatenate([np.zeros(len(e_s)), np.full(len(e_r), L * hr)])
+    if dt is None:
+        dt = 0.04 / n
+    return Scene(dim=3, n=(n, n, n), rho=rho, mu=mu, dt=dt, steps=steps, X=X, edges=edges, kappa=kappa,
+                 rest=rest, kernel=kernel, name=f"3D cylinder {n}^3, {ns}x{nr} markers")
+
+
+def tiled_ellipses_2d(tiles=2, n_per_tile=32, r1=5 / 28, r2=7 / 20, sigma=1.0, mu=0.01, rho=1.0, dt=None,
+                      steps=100, kernel="peskin4") -> Scene:
+    """tiles x tiles copies of the thin ellipse of Sec. 5.1, one per unit
+    tile of the periodic box [0, tiles]^2 (Sec. 6.3), with spacing h_s = 4h/19
+    along each ellipse; the fluid starts with the uniform background velocity
+    (1/2, sqrt(3)/2) set through Scene.extra['u0'].  Default dt = 0.01 h."""
+    n = tiles * n_per_tile
+    h = tiles / n
+    perim = np.pi * (3 * (r1 + r2) - np.sqrt((3 * r1 + r2) * (r1 + 3 * r2)))  # Ramanujan
+    ns = int(round(perim / (4 * h / 19)))
+    Xs, Es, Ks, Rs = [], [], [], []
+    for ty in range(tiles):
+        for tx in range(tiles):
+            X = ellipse_points(ns, r1, r2, center=(tx + 0.5, ty + 0.5))
+            e, k, rr = closed_fiber_connections(ns, sigma, 0.0, offset=len(Xs) * ns)
+            Xs.append(X)
+            Es.append(e)
+            Ks.append(k)
+            Rs.append(rr)
+    if dt is None:
+        dt = 0.01 * h
+    u0 = np.zeros((2, n, n))
+    u0[0] = 0.5
+    u0[1] = np.sqrt(3.0) / 2
+    return Scene(dim=2, n=(n, n), rho=rho, mu=mu, dt=dt, steps=steps, X=np.concatenate(Xs),
+                 edges=np.concatenate(Es), kappa=np.concatenate(Ks), rest=np.concatenate(Rs), H=float(tiles),
+                 kernel=kernel, name=f"2D {tiles}x{tiles} tiled ellipses {n}^2", extra={"u0": u0})
+
+
+def ensemble_members(count=48, seed=DEFAULT_SEED, sizes=(48, 64, 96, 128), dt128=5e-4):
+    """Independent 3D runs: grid N uniform over `sizes`, one ellipsoidal
+    membrane (semi-axes 0.2/0.25/0.3, icosahedral nu = N/2, about 2 markers per
+    h), stiffness sigma log-uniform in [0.1, 10], viscosity mu uniform in
+    [0.01, 0.1], dt = dt128 (128/N) min(1, sigma^-1/2)."""
+    g = rng(seed)
+    meshes = {}
+    out = []
+    for _ in range(count):
+        n = int(g.choice(sizes))
+        sigma = float(np.exp(g.uniform(np.log(0.1), np.log(10.0))))
+        mu = float(g.uniform(0.01, 0.1))
+        nu = n // 2
+        if nu not in meshes:
+            meshes[nu] = icosphere(nu)
+        V, T, E = meshes[nu]
+        X = V * np.array([0.2, 0.25, 0.3])[None, :] + 0.5
+        dt = dt128 * (128.0 / n) * min(1.0, sigma ** -0.5)
+        out.append(Scene(dim=3, n=(n, n, n), rho=1.0, mu=mu, dt=dt, steps=100, X=X, edges=E,
+                         kappa=np.full(E.shape[0], sigma), rest=np.zeros(E.shape[0]), tris=T,
+                         name=f"ensemble member {n}^3 sigma={sigma:.3g} mu={mu:.3g}"))
+    return out
+
+
+def random_ellipsoids_3d(n=512, count=8, nu=80, seed=DEFAULT_SEED, mu=0.01, dt=3.125e-5, steps=50,
+                         axes_range=(0.05, 0.1), sigma=1.0) -> Scene:
+    """`count` ellipsoidal membranes with semi-axes uniform in axes_range,
+    uniformly random orientations (normalised Gaussian quaternions) and
+    centres drawn by rejection until every pair is farther apart (periodic
+    distance) than the sum of their largest semi-axes plus 4h of the 512^3 grid
+    (the same bodies at every n); icosahedral meshes of frequency nu
+    (10 nu^2 + 2 markers each).  dt = 3.125e-5 is the largest of 1.25e-4,
+    6.25e-5 and 3.125e-5 that stays stable for 50 steps at 512^3 (1.25e-4
+    overflows within 30 steps; 6.25e-5 shows a growing divergence)."""
+    g = rng(seed)
+    V, T, E = icosphere(nu)
+    h = 1.0 / 512
+    bodies = []
+    while len(bodies) < count:
+        axes = g.uniform(*axes_range, size=3)
+        c = g.uniform(0, 1, size=3)
+        ok = True
+        for c2, a2 in bodies:
+            dvec = c - c2
+            dvec -= np.round(dvec)
+            if np.linalg.norm(dvec) <= axes.max() + a2.max() + 4 * h:
+                ok = False
+                break
+        if ok:
+            bodies.append((c, axes))
+    Xs, Es, Ts = [], [], []
+    for i, (c, axes) in enumerate(bodies):
+        R = random_rotation(g)
+        Xs.append((V * axes[None, :]) @ R.T + c[None, :])
+        Es.append(E + i * V.shape[0])
+        Ts.append(T + i * V.shape[0])
+    Eall = np.concatenate(Es).astype(np.int32)
+    return Scene(dim=3, n=(n, n, n), rho=1.0, mu=mu, dt=dt, steps=steps, X=np.concatenate(Xs), edges=Eall,
+                 kappa=np.full(Eall.shape[0], sigma), rest=np.zeros(Eall.shape[0]),
+                 tris=np.concatenate(Ts).astype(np.int32),
+                 name=f"3D {count} random ellipsoids {n}^3, nu={nu}")

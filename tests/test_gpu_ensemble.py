@@ -1,0 +1,67 @@
+"""Ensembles (members with different grids, stiffnesses and viscosities
+advanced by one graph launch per step) give the same states as the members
+stepped one by one, and match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1305_3976_gb300 as ib
+from paper_1305_3976_gb300 import inputs as I
+
+from test_gpu_step import compare, make_pair, psi_bound, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _grid(sc, prec):
+    g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, precision=prec, rotate_split=True)
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+    return g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ensemble_equals_members_stepped_alone(prec):
+    members = I.ensemble_members(count=5, sizes=(16, 24, 32))
+    ens_grids = [_grid(sc, prec) for sc in members]
+    solo = [_grid(sc, prec) for sc in members]
+    ens = ib.Ensemble(ens_grids)
+    ens.step(1)
+    ens.step(6)
+    for g in solo:
+        g.step(7)
+    tol = 1e-12 if prec == "fp64" else 1e-5     # atomics reorder the spread sums
+    for a, b in zip(ens_grids, solo):
+        fa, fb = a.fields(), b.fields()
+        for k in ("u", "v", "w", "p"):
+            assert rel(fa[k], fb[k]) < tol, (k, rel(fa[k], fb[k]))
+        assert np.max(np.abs(a.markers() - b.markers())) < (1e-13 if prec == "fp64" else 1e-7)
+    # members can be stepped on their own afterwards
+    ens_grids[0].step(1)
+    ens.close()
+    for g in ens_grids + solo:
+        g.close()
+
+
+def test_ensemble_member_matches_oracle():
+    sc = I.ensemble_members(count=3, sizes=(16, 24))[1]
+    ora, g = make_pair(sc, "fp64")
+    other = _grid(I.ensemble_members(count=1, sizes=(32,), seed=7)[0], "fp64")
+    ens = ib.Ensemble([other, g])
+    ora.step(4)
+    ens.step(4)
+    e = compare(ora, g)
+    assert e["u"] < psi_bound(sc, 4) and e["p"] < psi_bound(sc, 4), e
+    assert e["X"] < 1e-13
+    ens.close()
+    g.close()
+    other.close()
+
+
+def test_ensemble_rejects_mismatched_members():
+    a = ib.Grid(3, 16, precision="fp32")
+    b = ib.Grid(2, 16, precision="fp32")
+    with pytest.raises(ib.IBError) as ex:
+        ib.Ensemble([a, b])
+    assert ex.value.code == ib.IB_ERR_STATE
+    a.close()
+    b.close()
