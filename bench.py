@@ -280,6 +280,7 @@ def run_ours(args, rank, world, local):
     ab = kernel_bytes(dom, cells, nm, ne, w)
     achieved = ab / (per_launch[dom] * 1e-3) / 1e9
     diag = g.diagnostics()
+    tuned = g.sweep_configs()
     g.close()
 
     out = {
@@ -291,6 +292,9 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "steps_per_s": 1e3 / ms_step * world,
         "kernels_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+        "sweep_configs": {"x": {"id": tuned[0][0], "ctas_per_sm": tuned[0][3]},
+                          **{ax: {"id": t[0], "vector": t[1], "chunk": t[2], "warps_per_line": t[3]}
+                             for ax, t in zip(("y", "z"), tuned[1:])}},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom)},

@@ -210,6 +210,15 @@ int ib_split_solve(int precision, int dim, const int n[3], const double r[3], co
 int ib_split_solve_noalloc(int precision, int dim, const int n[3], const double r[3], const void *f,
                            void *psi, void *stream);
 
+/* The line-solve configuration a grid chose for `axis` (0..dim-1).  On its
+ * first step (or first call that needs the device state) a grid times every
+ * candidate configuration of its sweeps per axis on its own scratch fields and
+ * keeps the fastest.  cfg[4] receives: the configuration id, then for y/z
+ * lines the vector width (adjacent x lines per thread), the chunk length and
+ * the warps per line, or for x lines 1, the warps per CTA (8) and the cap on
+ * CTAs per SM.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_sweep_config(ib_grid_t g, int axis, int cfg[4]);
+
 /* Run n_steps steps with every kernel launched on its own and timed by CUDA
  * events on the grid's stream; kernel_ms[i] receives the total milliseconds
  * of kernel slot i (at most max_kernels slots, *n_kernels gets the count) and

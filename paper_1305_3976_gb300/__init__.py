@@ -26,7 +26,8 @@ FIELD_BITS = ("u", "v", "w", "p", "psi", "div")
 EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_read_fields", "ib_read_markers",
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
-           "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble")
+           "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
+           "ib_sweep_config")
 
 
 class ib_grid_desc(C.Structure):
@@ -75,6 +76,7 @@ def lib():
         L.ib_create_ensemble.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
         L.ib_ensemble_step.argtypes = [vp, C.c_int]
         L.ib_destroy_ensemble.argtypes = [vp]
+        L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
         for name in EXPORTS:
@@ -220,6 +222,12 @@ def ib_split_solve_noalloc(precision, dim, n, r, f, psi, stream="current"):
            "ib_split_solve_noalloc")
 
 
+def ib_sweep_config(g, axis):
+    cfg = (C.c_int * 4)()
+    _check(lib().ib_sweep_config(g, axis, cfg), "ib_sweep_config")
+    return tuple(cfg)
+
+
 def ib_profile_step(g, n_steps):
     ms = (C.c_float * 16)()
     nk = C.c_int()
@@ -307,6 +315,10 @@ class Grid:
 
     def profile(self, n_steps=1):
         return ib_profile_step(self.h, n_steps)
+
+    def sweep_configs(self):
+        """Autotuned line-solve configuration per axis: (id, a, b, c)."""
+        return [ib_sweep_config(self.h, a) for a in range(self.dim)]
 
     def close(self):
         if self.h:

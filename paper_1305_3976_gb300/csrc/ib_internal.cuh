@@ -97,7 +97,10 @@ struct MarkerArgs {
 
 // launchers (return cudaError_t of the launch)
 template <typename T>
-cudaError_t launch_sweep(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s);
+cudaError_t launch_sweep(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s,
+                         int cfg = -1);
+int sweep_candidates(int axis, int nl, int nx, bool dbl, int *out, int max);
+void sweep_config_shape(int axis, int cfg, int *a, int *b, int *c);
 template <typename T>
 cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s);
 template <typename T>

@@ -62,6 +62,69 @@ __device__ __forceinline__ T div_prologue(const SweepArgs<T> &a, long long o, in
   return a.pro_scale * dnew;
 }
 
+// VW consecutive elements (VW = 1, 2, 4), VW-aligned
+template <int VW, typename T>
+__device__ __forceinline__ void ldv(const T *p, T (&v)[VW]) {
+  if (VW == 4) {
+    T t[4];
+    ld4(p, t);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) v[i] = t[i];
+  } else if (VW == 2) {
+    if (sizeof(T) == 4) {
+      const float2 t = *reinterpret_cast<const float2 *>(p);
+      v[0] = (T)t.x;
+      v[VW - 1] = (T)t.y;
+    } else {
+      const double2 t = *reinterpret_cast<const double2 *>(p);
+      v[0] = (T)t.x;
+      v[VW - 1] = (T)t.y;
+    }
+  } else {
+    v[0] = *p;
+  }
+}
+template <int VW, typename T>
+__device__ __forceinline__ void stv(T *p, const T (&v)[VW]) {
+  if (VW == 4) {
+    T t[4] = {v[0], v[VW > 1 ? 1 : 0], v[VW > 2 ? 2 : 0], v[VW > 3 ? 3 : 0]};
+    st4(p, t);
+  } else if (VW == 2) {
+    if (sizeof(T) == 4) *reinterpret_cast<float2 *>(p) = make_float2((float)v[0], (float)v[VW - 1]);
+    else *reinterpret_cast<double2 *>(p) = make_double2((double)v[0], (double)v[VW - 1]);
+  } else {
+    *p = v[0];
+  }
+}
+
+// Per-lane constants of a full-length x line (n = 128 R): loaded once per
+// warp and reused for every line it solves.
+template <typename T, int R>
+struct XLineCoef {
+  T lam, l2, l3, l4, inv_c, inv_1m;
+  T gk[5];      // lam^(4 * 2^k)
+  T gf, gb;     // gains of lanes 0..lane and lane..31
+  T pf[R], pb[R];  // lam^(i0) and lam^(n - i0 - 4) of this lane's chunks
+  __device__ __forceinline__ void load(const LineCoef<T> &co, int n, int lane) {
+    const T *pw = co.pw;
+    lam = co.lam;
+    inv_c = co.inv_c;
+    inv_1m = co.inv_1m;
+    l2 = ld_ro(pw + 2);
+    l3 = ld_ro(pw + 3);
+    l4 = ld_ro(pw + 4);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) gk[q] = ld_ro(pw + (4 << q));
+    gf = ld_ro(pw + 4 * (lane + 1));
+    gb = ld_ro(pw + 4 * (32 - lane));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      pf[r] = ld_ro(pw + (r * 32 + lane) * 4);
+      pb[r] = ld_ro(pw + (n - (r * 32 + lane) * 4 - 4));
+    }
+  }
+};
+
 // Solve one x line held by a warp: v[r][e] is element (32 r + lane) * 4 + e.
 template <typename T, int R>
 __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, int lane, T (&v)[R][4]) {
@@ -141,15 +204,8 @@ __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, in
 // lam^(4 2^k); the scan then shuffles only the partial sums and all powers
 // live in registers.
 template <typename T, int R>
-__device__ __forceinline__ void solve_line_warp_full(const LineCoef<T> &co, int n, int lane, T (&v)[R][4]) {
-  const T lam = co.lam;
-  const T *pw = co.pw;
-  const T l1 = lam, l2 = ld_ro(pw + 2), l3 = ld_ro(pw + 3), l4 = ld_ro(pw + 4);
-  T gk[5];  // lam^(4 * 2^k), k = 0..4
-#pragma unroll
-  for (int q = 0; q < 5; ++q) gk[q] = ld_ro(pw + (4 << q));
-  const T glane_f = ld_ro(pw + 4 * (lane + 1));   // gain of lanes 0..lane
-  const T glane_b = ld_ro(pw + 4 * (32 - lane));  // gain of lanes lane..31
+__device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, int lane, T (&v)[R][4]) {
+  const T lam = c.lam;
   T cin[R];
   // forward factor
   T carry = T(0);
@@ -163,21 +219,21 @@ __device__ __forceinline__ void solve_line_warp_full(const LineCoef<T> &co, int 
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const T su = __shfl_up_sync(IBG_FULL, s, 1 << q);
-      if (lane >= (1 << q)) s = fma(su, gk[q], s);
+      if (lane >= (1 << q)) s = fma(su, c.gk[q], s);
     }
-    const T S = fma(glane_f, carry, s);
+    const T S = fma(c.gf, carry, s);
     const T Sx = __shfl_up_sync(IBG_FULL, S, 1);
     cin[r] = lane == 0 ? carry : Sx;
     carry = __shfl_sync(IBG_FULL, S, 31);
   }
-  T K = carry * co.inv_1m;
+  T K = carry * c.inv_1m;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const T t = fma(ld_ro(pw + (r * 32 + lane) * 4), K, cin[r]);
-    v[r][0] = fma(l1, t, v[r][0]);
-    v[r][1] = fma(l2, t, v[r][1]);
-    v[r][2] = fma(l3, t, v[r][2]);
-    v[r][3] = fma(l4, t, v[r][3]);
+    const T t = fma(c.pf[r], K, cin[r]);
+    v[r][0] = fma(lam, t, v[r][0]);
+    v[r][1] = fma(c.l2, t, v[r][1]);
+    v[r][2] = fma(c.l3, t, v[r][2]);
+    v[r][3] = fma(c.l4, t, v[r][3]);
   }
   // backward factor
   carry = T(0);
@@ -191,35 +247,29 @@ __device__ __forceinline__ void solve_line_warp_full(const LineCoef<T> &co, int 
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const T sd = __shfl_down_sync(IBG_FULL, s, 1 << q);
-      if (lane + (1 << q) < 32) s = fma(sd, gk[q], s);
+      if (lane + (1 << q) < 32) s = fma(sd, c.gk[q], s);
     }
-    const T S = fma(glane_b, carry, s);
+    const T S = fma(c.gb, carry, s);
     const T Sx = __shfl_down_sync(IBG_FULL, S, 1);
     cin[r] = lane == 31 ? carry : Sx;
     carry = __shfl_sync(IBG_FULL, S, 0);
   }
-  K = carry * co.inv_1m;
+  K = carry * c.inv_1m;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const T t = fma(ld_ro(pw + (n - (r * 32 + lane) * 4 - 4)), K, cin[r]);
-    v[r][0] = fma(l4, t, v[r][0]) * co.inv_c;
-    v[r][1] = fma(l3, t, v[r][1]) * co.inv_c;
-    v[r][2] = fma(l2, t, v[r][2]) * co.inv_c;
-    v[r][3] = fma(l1, t, v[r][3]) * co.inv_c;
+    const T t = fma(c.pb[r], K, cin[r]);
+    v[r][0] = fma(c.l4, t, v[r][0]) * c.inv_c;
+    v[r][1] = fma(c.l3, t, v[r][1]) * c.inv_c;
+    v[r][2] = fma(c.l2, t, v[r][2]) * c.inv_c;
+    v[r][3] = fma(lam, t, v[r][3]) * c.inv_c;
   }
 }
 
-// one warp per x line; blockIdx.y selects the field
+// one x line per warp and loop iteration; blockIdx.y selects the field
 template <typename T, int R, int PRO, int EPI, bool FULL>
-__global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineCoef<T, R> &xc, T *F, const T *Fin,
+                                             int comp, long long line, int lane) {
   const int nx = a.n[0], ny = a.n[1];
-  const long long nlines = (long long)ny * (a.dim == 3 ? a.n[2] : 1);
-  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (line >= nlines) return;  // uniform per warp
-  const int comp = blockIdx.y;
-  T *F = a.f[comp];
-  const T *Fin = a.fin[comp] ? a.fin[comp] : F;
   const int j = (int)(line % ny), k = (int)(line / ny);
   const long long base = line * nx;
   const bool vec = (nx & 3) == 0;
@@ -295,7 +345,7 @@ __global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
       }
     }
   }
-  if (FULL) solve_line_warp_full<T, R>(a.co, nx, lane, v);
+  if (FULL) solve_line_warp_full<T, R>(xc, lane, v);
   else solve_line_warp<T, R>(a.co, nx, lane, v);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -346,60 +396,98 @@ __global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
   }
 }
 
-// strided lines along axis 1 (y) or 2 (z); blockIdx.x: 32 x columns,
-// blockIdx.y: the remaining coordinate, blockIdx.z: the field.  FULL: the
-// line length is exactly W * CH, so no element needs a bounds test.
-// Element offsets fit in 32 bits (at most 512^3 elements per field).
-template <typename T, int CH, int W, int PRO, int EPI, bool FULL>
+template <typename T, int R, int PRO, int EPI, bool FULL>
+__global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int nx = a.n[0], ny = a.n[1];
+  const long long nlines = (long long)ny * (a.dim == 3 ? a.n[2] : 1);
+  const int comp = blockIdx.y;
+  T *F = a.f[comp];
+  const T *Fin = a.fin[comp] ? a.fin[comp] : F;
+  XLineCoef<T, R> xc;
+  if (FULL) xc.load(a.co, nx, lane);
+  // each warp solves lines warp, warp + W, ... (W warps in the grid)
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < nlines;
+       line += wstride)
+    sweep_x_line<T, R, PRO, EPI, FULL>(a, xc, F, Fin, comp, line, lane);
+}
+
+// strided lines along axis 1 (y) or 2 (z); a thread owns VW adjacent x
+// columns (VW-wide vector loads, so a warp reads 32 VW consecutive values of
+// a row); blockIdx.x: 32 VW x columns, blockIdx.y: the remaining coordinate,
+// blockIdx.z: the field.  FULL: the line length is exactly W * CH, so no
+// element needs a bounds test.  Element offsets fit in 32 bits (at most 512^3
+// elements per field).
+template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL>
 __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const int axis) {
-  __shared__ T sz[W][33];
+  __shared__ T sz[W][VW][33];
   __shared__ T lp[CH + 1];  // lam^0 .. lam^CH
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nx = a.n[0], ny = a.n[1];
-  const int x = blockIdx.x * 32 + lane;
+  const int x0 = (blockIdx.x * 32 + lane) * VW;
   const int other = blockIdx.y;
-  if (threadIdx.x <= CH) lp[threadIdx.x] = ld_ro(a.co.pw + threadIdx.x);
   const int comp = blockIdx.z;
+  if (threadIdx.x <= CH) lp[threadIdx.x] = ld_ro(a.co.pw + threadIdx.x);
   T *F = a.f[comp];
   const T *Fin = a.fin[comp] ? a.fin[comp] : F;
   const int nl = a.n[axis];
   const int stride = axis == 1 ? nx : nx * ny;
-  const int base = axis == 1 ? x + nx * ny * other : x + nx * other;
-  const bool xok = x < nx;
+  const int base = axis == 1 ? x0 + nx * ny * other : x0 + nx * other;
+  const bool xok = x0 < nx;  // nx is a multiple of VW
   const int start = w * CH;
   const int len = FULL ? CH : max(0, min(CH, nl - start));
   const T lam = a.co.lam;
   const T *pw = a.co.pw;
   const int o0 = base + start * stride;
-  T v[CH];
-  T pn[PRO == PRO_DIV ? CH : 1];
+  T v[CH][VW];
+  T pn[PRO == PRO_DIV ? CH : 1][VW];
   if (PRO == PRO_LOAD) {
 #pragma unroll
-    for (int e = 0; e < CH; ++e) v[e] = (xok && (FULL || e < len)) ? Fin[o0 + e * stride] : T(0);
+    for (int e = 0; e < CH; ++e) {
+      if (xok && (FULL || e < len)) ldv<VW>(Fin + o0 + e * stride, v[e]);
+      else {
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[e][c] = T(0);
+      }
+    }
   } else {
     // Step 3e right-hand side -rho/dt D.u^{n+1}; the new D.u and p are stored
-    // after every load of the chunk (see below)
-    const int dx = x + 1 == nx ? 1 - nx : 1;
+    // after every load of the chunk
     const int nz = a.dim == 3 ? a.n[2] : 1;
     const int jo = axis == 1 ? -1 : other, ko = axis == 1 ? other : -1;  // fixed coordinate
-    const int ld_y = nx, ld_z = nx * ny;
+    const int xe = x0 + VW == nx ? -x0 : VW;   // offset of the face after the last column
 #pragma unroll
     for (int e = 0; e < CH; ++e) {
-      v[e] = T(0);
-      pn[PRO == PRO_DIV ? e : 0] = T(0);
+#pragma unroll
+      for (int c = 0; c < VW; ++c) v[e][c] = pn[PRO == PRO_DIV ? e : 0][c] = T(0);
       if (xok && (FULL || e < len)) {
         const int t = start + e;
         const int j = axis == 1 ? t : jo, k = axis == 1 ? ko : t;
         const int o = o0 + e * stride;
-        const int dy = j + 1 == ny ? ld_y * (1 - ny) : ld_y;
-        T d = (ld_ro(a.u[0] + o + dx) - ld_ro(a.u[0] + o)) * a.inv_h[0];
-        d += (ld_ro(a.u[1] + o + dy) - ld_ro(a.u[1] + o)) * a.inv_h[1];
+        const int dy = j + 1 == ny ? nx * (1 - ny) : nx;
+        T u0[VW], v0[VW], v1[VW], dv[VW], pv[VW];
+        ldv<VW>(a.u[0] + o, u0);
+        const T ue = ld_ro(a.u[0] + o + xe);
+        ldv<VW>(a.u[1] + o, v0);
+        ldv<VW>(a.u[1] + o + dy, v1);
+        ldv<VW>(a.div + o, dv);
+        ldv<VW>(a.p + o, pv);
+        T w0[VW], w1[VW];
         if (a.dim == 3) {
-          const int dz = k + 1 == nz ? ld_z * (1 - nz) : ld_z;
-          d += (ld_ro(a.u[2] + o + dz) - ld_ro(a.u[2] + o)) * a.inv_h[2];
+          const int dz = k + 1 == nz ? nx * ny * (1 - nz) : nx * ny;
+          ldv<VW>(a.u[2] + o, w0);
+          ldv<VW>(a.u[2] + o + dz, w1);
         }
-        pn[PRO == PRO_DIV ? e : 0] = a.p[o] - a.chi_mu_half * (d + a.div[o]);
-        v[e] = a.pro_scale * d;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+          const T up = c + 1 < VW ? u0[c + 1 < VW ? c + 1 : 0] : ue;
+          T d = (up - u0[c]) * a.inv_h[0];
+          d += (v1[c] - v0[c]) * a.inv_h[1];
+          if (a.dim == 3) d += (w1[c] - w0[c]) * a.inv_h[2];
+          pn[PRO == PRO_DIV ? e : 0][c] = pv[c] - a.chi_mu_half * (d + dv[c]);
+          v[e][c] = a.pro_scale * d;
+        }
       }
     }
     if (xok) {
@@ -408,75 +496,165 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) {
           const int o = o0 + e * stride;
-          a.div[o] = v[e] * inv_scale;
-          a.p[o] = pn[PRO == PRO_DIV ? e : 0];
+          T dnew[VW];
+#pragma unroll
+          for (int c = 0; c < VW; ++c) dnew[c] = v[e][c] * inv_scale;
+          stv<VW>(a.div + o, dnew);
+          stv<VW>(a.p + o, pn[PRO == PRO_DIV ? e : 0]);
         }
     }
   }
+  __syncthreads();  // lp
+  const T gCH = lp[CH];
   // forward factor (I - lam S) y = b: local pass, chunk scan, correction
-  T z = T(0);
+  {
+    T z[VW];
 #pragma unroll
-  for (int e = 0; e < CH; ++e)
-    if (FULL || e < len) { z = fma(lam, z, v[e]); v[e] = z; }
-  sz[w][lane] = z;
-  __syncthreads();
-  T cin = T(0);
-  for (int q = 0; q < w; ++q) cin = fma(cin, FULL ? lp[CH] : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][lane]);
-  T tot = cin;
-  for (int q = w; q < W; ++q) tot = fma(tot, FULL ? lp[CH] : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][lane]);
-  T t = fma(ld_ro(pw + min(start, nl)), tot * a.co.inv_1m, cin);
-#pragma unroll
-  for (int e = 0; e < CH; ++e)
-    if (FULL || e < len) v[e] = fma(lp[e + 1], t, v[e]);
-  __syncthreads();
-  // backward factor (I - lam S^{-1}) x = y
-  z = T(0);
-#pragma unroll
-  for (int e = CH - 1; e >= 0; --e)
-    if (FULL || e < len) { z = fma(lam, z, v[e]); v[e] = z; }
-  sz[w][lane] = z;
-  __syncthreads();
-  cin = T(0);
-  for (int q = W - 1; q > w; --q) cin = fma(cin, FULL ? lp[CH] : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][lane]);
-  tot = cin;
-  for (int q = w; q >= 0; --q) tot = fma(tot, FULL ? lp[CH] : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][lane]);
-  if (FULL || len > 0) {
-    t = fma(ld_ro(pw + (nl - start - len)), tot * a.co.inv_1m, cin);
+    for (int c = 0; c < VW; ++c) z[c] = T(0);
 #pragma unroll
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) {
-        const int pe = FULL ? CH - e : max(0, len - e);
-        v[e] = fma(lp[pe], t, v[e]) * a.co.inv_c;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[e][c] = z[c] = fma(lam, z[c], v[e][c]);
       }
+#pragma unroll
+    for (int c = 0; c < VW; ++c) sz[w][c][lane] = z[c];
+  }
+  __syncthreads();
+  const T pstart = ld_ro(pw + min(start, nl));
+#pragma unroll
+  for (int c = 0; c < VW; ++c) {
+    T cin = T(0);
+    for (int q = 0; q < w; ++q) cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+    T tot = cin;
+    for (int q = w; q < W; ++q) tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+    const T t = fma(pstart, tot * a.co.inv_1m, cin);
+#pragma unroll
+    for (int e = 0; e < CH; ++e)
+      if (FULL || e < len) v[e][c] = fma(lp[e + 1], t, v[e][c]);
+  }
+  __syncthreads();
+  // backward factor (I - lam S^{-1}) x = y
+  {
+    T z[VW];
+#pragma unroll
+    for (int c = 0; c < VW; ++c) z[c] = T(0);
+#pragma unroll
+    for (int e = CH - 1; e >= 0; --e)
+      if (FULL || e < len) {
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[e][c] = z[c] = fma(lam, z[c], v[e][c]);
+      }
+#pragma unroll
+    for (int c = 0; c < VW; ++c) sz[w][c][lane] = z[c];
+  }
+  __syncthreads();
+  if (FULL || len > 0) {
+    const T pend = ld_ro(pw + (nl - start - len));
+#pragma unroll
+    for (int c = 0; c < VW; ++c) {
+      T cin = T(0);
+      for (int q = W - 1; q > w; --q)
+        cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+      T tot = cin;
+      for (int q = w; q >= 0; --q)
+        tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+      const T t = fma(pend, tot * a.co.inv_1m, cin);
+#pragma unroll
+      for (int e = 0; e < CH; ++e)
+        if (FULL || e < len) {
+          const int pe = FULL ? CH - e : max(0, len - e);
+          v[e][c] = fma(lp[pe], t, v[e][c]) * a.co.inv_c;
+        }
+    }
   }
   if (!xok) return;
   if (EPI == EPI_STORE) {
 #pragma unroll
     for (int e = 0; e < CH; ++e)
-      if (FULL || e < len) F[o0 + e * stride] = v[e];
+      if (FULL || e < len) stv<VW>(F + o0 + e * stride, v[e]);
   } else {
     // scratch / psi stores first, then every load of the old values, then the
     // sums: no load waits behind a store
     T *tgt = EPI == EPI_ADDU ? a.uo[comp] : a.p;
+    const T zero[VW] = {};
 #pragma unroll
     for (int e = 0; e < CH; ++e)
-      if (FULL || e < len) F[o0 + e * stride] = EPI == EPI_ADDU ? T(0) : v[e];  // clear scratch / store psi
+      if (FULL || e < len) {
+        if (EPI == EPI_ADDU) stv<VW>(F + o0 + e * stride, zero);  // clear the scratch
+        else stv<VW>(F + o0 + e * stride, v[e]);                   // psi
+      }
 #pragma unroll
     for (int e = 0; e < CH; ++e)
-      if (FULL || e < len) v[e] += tgt[o0 + e * stride];
+      if (FULL || e < len) {
+        T old[VW];
+        ldv<VW>(tgt + o0 + e * stride, old);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[e][c] += old[c];
+      }
 #pragma unroll
     for (int e = 0; e < CH; ++e)
-      if (FULL || e < len) tgt[o0 + e * stride] = v[e];
+      if (FULL || e < len) stv<VW>(tgt + o0 + e * stride, v[e]);
   }
 }
 
-// line lengths 8 <= n <= 512 (checked by the caller)
+// Sweep configurations.  Strided lines (axes 1, 2): VW adjacent x columns
+// per thread, CH elements per warp chunk, W warps per line.  x lines: the
+// grid is capped at XCAP[i] * 152 CTAs of 8 warps (warps loop over lines).
+struct StridedCfg {
+  int vw, ch, w;
+};
+__host__ __device__ constexpr StridedCfg strided_cfg(int i) {
+  return i == 0 ? StridedCfg{1, 8, 8}
+       : i == 1 ? StridedCfg{2, 8, 8}
+       : i == 2 ? StridedCfg{4, 8, 8}
+       : i == 3 ? StridedCfg{1, 16, 8}
+       : i == 4 ? StridedCfg{2, 8, 16}
+       : i == 5 ? StridedCfg{4, 8, 16}
+       : i == 6 ? StridedCfg{1, 16, 16}
+       : i == 7 ? StridedCfg{2, 16, 16}
+       : i == 8 ? StridedCfg{1, 16, 32}
+       : i == 9 ? StridedCfg{2, 16, 32}
+                : StridedCfg{1, 32, 16};
+}
+constexpr int kStridedCfgs = 11;
+constexpr int kXCaps = 4;
+__host__ __device__ constexpr int xcap(int i) { return i == 0 ? 2 : i == 1 ? 4 : i == 2 ? 8 : 1 << 20; }
+
+// Whether strided configuration i can run this sweep: it must cover the line
+// with less than twice its length (n <= CH W < 2n; the smallest shape,
+// CH = 8 and W = 8, covers every shorter line), n_x must be a multiple of VW,
+// and VW CH is at most 32 values per thread in FP32, 16 for the divergence
+// prologue and in FP64 (32 in FP64 with VW = 1 and W = 16).
+inline bool strided_cfg_ok(int i, int nl, int nx, bool dbl, bool div) {
+  const StridedCfg c = strided_cfg(i);
+  const bool smallest = c.ch == 8 && c.w == 8;
+  if (c.ch * c.w < nl || (!smallest && c.ch * c.w >= 2 * nl) || nx % c.vw) return false;
+  if (dbl) return c.vw == 1;
+  return c.vw * c.ch <= (div ? 16 : 32);
+}
+
+// The default choice (no autotuning): the first valid configuration in the
+// order of preference below.
+inline int strided_cfg_default(int nl, int nx, bool dbl, bool div) {
+  static const int pref_f[] = {3, 0, 6, 1, 4, 7, 9, 2, 5, 8, 10};
+  static const int pref_d[] = {0, 3, 6, 10, 8};
+  const int *pref = dbl ? pref_d : pref_f;
+  const int np = dbl ? 5 : 11;
+  for (int k = 0; k < np; ++k)
+    if (strided_cfg_ok(pref[k], nl, nx, dbl, div)) return pref[k];
+  return -1;
+}
+
+// line lengths 8 <= n <= 512 (checked by the caller); cfg < 0: default
 template <typename T, int PRO, int EPI>
-cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStream_t s) {
+cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStream_t s, int cfg) {
   const int nl = a.n[axis];
   if (axis == 0) {
     const long long nlines = (long long)a.n[1] * (a.dim == 3 ? a.n[2] : 1);
-    dim3 grid((unsigned)((nlines + 7) / 8), nfields);
+    const long long ctas = (nlines + 7) / 8;
+    const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
+    dim3 grid((unsigned)(ctas < cap ? ctas : cap), nfields);  // warps loop over lines
     if (nl == 128) k_sweep_x<T, 1, PRO, EPI, true><<<grid, 256, 0, s>>>(a);
     else if (nl < 128) k_sweep_x<T, 1, PRO, EPI, false><<<grid, 256, 0, s>>>(a);
     else if (nl == 256) k_sweep_x<T, 2, PRO, EPI, true><<<grid, 256, 0, s>>>(a);
@@ -485,28 +663,43 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
     else k_sweep_x<T, 4, PRO, EPI, false><<<grid, 256, 0, s>>>(a);
   } else {
     const int other = axis == 1 ? (a.dim == 3 ? a.n[2] : 1) : a.n[1];
-    dim3 grid((unsigned)((a.n[0] + 31) / 32), other, nfields);
-    if (nl == 64) k_sweep_s<T, 8, 8, PRO, EPI, true><<<grid, 256, 0, s>>>(a, axis);
-    else if (nl < 64) k_sweep_s<T, 8, 8, PRO, EPI, false><<<grid, 256, 0, s>>>(a, axis);
-    else if (nl == 128) k_sweep_s<T, 16, 8, PRO, EPI, true><<<grid, 256, 0, s>>>(a, axis);
-    else if (nl < 128) k_sweep_s<T, 16, 8, PRO, EPI, false><<<grid, 256, 0, s>>>(a, axis);
-    else if (nl == 256) k_sweep_s<T, 16, 16, PRO, EPI, true><<<grid, 512, 0, s>>>(a, axis);
-    else if (nl < 256) k_sweep_s<T, 16, 16, PRO, EPI, false><<<grid, 512, 0, s>>>(a, axis);
-    else if constexpr (sizeof(T) == 8) {  // FP64: fewer, longer chunks keep 512-thread CTAs within registers
-      if (nl == 512) k_sweep_s<T, 32, 16, PRO, EPI, true><<<grid, 512, 0, s>>>(a, axis);
-      else k_sweep_s<T, 32, 16, PRO, EPI, false><<<grid, 512, 0, s>>>(a, axis);
-    } else if (nl == 512) k_sweep_s<T, 16, 32, PRO, EPI, true><<<grid, 1024, 0, s>>>(a, axis);
-    else k_sweep_s<T, 16, 32, PRO, EPI, false><<<grid, 1024, 0, s>>>(a, axis);
+    const int nx = a.n[0];
+    const bool dbl = sizeof(T) == 8, div = PRO == PRO_DIV;
+    if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl, div))
+      cfg = strided_cfg_default(nl, nx, dbl, div);
+    auto grid = [&](int v) { return dim3((unsigned)((nx / v + 31) / 32), other, nfields); };
+#define IBG_S(I)                                                                                        \
+  case I: {                                                                                             \
+    constexpr StridedCfg c = strided_cfg(I);                                                            \
+    if (nl == c.ch * c.w)                                                                               \
+      k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true><<<grid(c.vw), 32 * c.w, 0, s>>>(a, axis);          \
+    else k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false><<<grid(c.vw), 32 * c.w, 0, s>>>(a, axis);      \
+  } break;
+    if constexpr (sizeof(T) == 8) {
+      switch (cfg) { IBG_S(0) IBG_S(3) IBG_S(6) IBG_S(8) IBG_S(10) default: return cudaErrorInvalidValue; }
+    } else if constexpr (PRO == PRO_DIV) {
+      switch (cfg) {
+        IBG_S(0) IBG_S(1) IBG_S(3) IBG_S(4) IBG_S(6) IBG_S(8) IBG_S(10)
+        default: return cudaErrorInvalidValue;
+      }
+    } else {
+      switch (cfg) {
+        IBG_S(0) IBG_S(1) IBG_S(2) IBG_S(3) IBG_S(4) IBG_S(5) IBG_S(6) IBG_S(7) IBG_S(8) IBG_S(9) IBG_S(10)
+        default: return cudaErrorInvalidValue;
+      }
+    }
+#undef IBG_S
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_sweep_impl(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s) {
-  if (pro == PRO_LOAD && epi == EPI_STORE) return launch_sweep_t<T, PRO_LOAD, EPI_STORE>(axis, nfields, a, s);
-  if (pro == PRO_LOAD && epi == EPI_ADDU) return launch_sweep_t<T, PRO_LOAD, EPI_ADDU>(axis, nfields, a, s);
-  if (pro == PRO_DIV && epi == EPI_STORE) return launch_sweep_t<T, PRO_DIV, EPI_STORE>(axis, nfields, a, s);
-  if (pro == PRO_LOAD && epi == EPI_P) return launch_sweep_t<T, PRO_LOAD, EPI_P>(axis, nfields, a, s);
+cudaError_t launch_sweep_impl(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s,
+                              int cfg) {
+  if (pro == PRO_LOAD && epi == EPI_STORE) return launch_sweep_t<T, PRO_LOAD, EPI_STORE>(axis, nfields, a, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_ADDU) return launch_sweep_t<T, PRO_LOAD, EPI_ADDU>(axis, nfields, a, s, cfg);
+  if (pro == PRO_DIV && epi == EPI_STORE) return launch_sweep_t<T, PRO_DIV, EPI_STORE>(axis, nfields, a, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_P) return launch_sweep_t<T, PRO_LOAD, EPI_P>(axis, nfields, a, s, cfg);
   return cudaErrorInvalidValue;
 }
 

@@ -166,6 +166,8 @@ struct ib_grid_s {
   int64_t step = 0;
   bool div_valid = false;
   bool loc_valid = false;       // locI holds the grid locations of the current X
+  bool tuned = false;
+  int tune[3] = {-1, -1, -1};   // sweep configuration per axis (autotuned)
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -265,7 +267,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   for (int st = 0; st < d; ++st) {
     const int ax = order[st];
     sa.co = coef_of<T>(g->coef[0][ax]);
-    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, st == d - 1 ? EPI_ADDU : EPI_STORE, d, sa, g->s));
+    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, st == d - 1 ? EPI_ADDU : EPI_STORE, d, sa, g->s, g->tune[ax]));
     if ((rc = mark(6 + st))) return rc;
   }
   // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
@@ -276,7 +278,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     sa.co = coef_of<T>(g->coef[1][ax]);
     const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
     const int epi = st == d - 1 ? EPI_P : EPI_STORE;
-    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s));
+    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s, g->tune[ax]));
     if ((rc = mark(9 + st))) return rc;
   }
   return IB_OK;
@@ -464,11 +466,68 @@ int ensure_loc(ib_grid_s *g) {
   return IB_OK;
 }
 
+// Autotuner: for every axis, time each candidate sweep configuration on the
+// d scratch fields (zero outside a step) with the plain load/store sweep,
+// 1 + 3 launches each, and keep the fastest; the step's sweeps along that
+// axis then use it.
+template <typename T>
+int autotune_t(ib_grid_s *g) {
+  const int d = g->dim;
+  SweepArgs<T> sa;
+  memset(&sa, 0, sizeof(sa));
+  for (int a = 0; a < 3; ++a) {
+    sa.f[a] = (T *)g->scr[a];
+    sa.n[a] = g->n[a];
+    sa.inv_h[a] = (T)(1.0 / g->h[a]);
+  }
+  sa.dim = d;
+  cudaEvent_t e0, e1;
+  IB_CUDA(cudaEventCreate(&e0));
+  IB_CUDA(cudaEventCreate(&e1));
+  int rc = IB_OK;
+  for (int ax = 0; ax < d && !rc; ++ax) {
+    sa.co = coef_of<T>(g->coef[0][ax]);
+    int cand[16];
+    const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 16);
+    float best = 1e30f;
+    for (int i = 0; i < nc && !rc; ++i) {
+      if (launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, cand[i]) != cudaSuccess) {
+        rc = fail(IB_ERR_CUDA, "autotune launch");
+        break;
+      }
+      cudaEventRecord(e0, g->s);
+      for (int r = 0; r < 3; ++r) launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, cand[i]);
+      cudaEventRecord(e1, g->s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(IB_ERR_CUDA, "autotune sync");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        g->tune[ax] = cand[i];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int autotune(ib_grid_s *g) {
+  if (g->tuned) return IB_OK;
+  int rc = g->prec == IB_FP32 ? autotune_t<float>(g) : autotune_t<double>(g);
+  g->tuned = true;
+  return rc;
+}
+
 int prepare(ib_grid_s *g) {
   int rc = upload_markers(g);
   if (rc) return rc;
   if ((rc = ensure_loc(g))) return rc;
   if ((rc = ensure_div(g))) return rc;
+  if ((rc = autotune(g))) return rc;
   // capture the step graph of every split-order phase up front so that no
   // instantiation happens between later steps
   const int phases = g->desc.rotate_split ? g->dim : 1;
@@ -687,6 +746,18 @@ int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels,
   for (int k = 0; k < nk && k < max_kernels; ++k) kernel_ms[k] = (float)tot[k];
   if (n_kernels) *n_kernels = nk < max_kernels ? nk : max_kernels;
   return leave(g);
+}
+
+int ib_sweep_config(ib_grid_t g, int axis, int *cfg) {
+  if (!g || !cfg || axis < 0 || axis >= g->dim) return fail(IB_ERR_ARG, "bad argument");
+  int rc = enter(g);
+  if (!rc) rc = prepare(g);
+  if (!rc) rc = leave(g);
+  if (rc) return rc;
+  const int id = g->tune[axis];
+  sweep_config_shape(axis, id, &cfg[1], &cfg[2], &cfg[3]);
+  cfg[0] = id;
+  return IB_OK;
 }
 
 const char *ib_kernel_name(int slot) {

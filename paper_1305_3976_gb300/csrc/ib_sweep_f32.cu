@@ -3,7 +3,35 @@
 
 namespace ibg {
 template <>
-cudaError_t launch_sweep<float>(int axis, int pro, int epi, int nfields, const SweepArgs<float> &a, cudaStream_t s) {
-  return launch_sweep_impl<float>(axis, pro, epi, nfields, a, s);
+cudaError_t launch_sweep<float>(int axis, int pro, int epi, int nfields, const SweepArgs<float> &a, cudaStream_t s,
+                               int cfg) {
+  return launch_sweep_impl<float>(axis, pro, epi, nfields, a, s, cfg);
+}
+}  // namespace ibg
+
+namespace ibg {
+// candidate sweep configurations for the autotuner (ids of strided_cfg for
+// axes 1, 2; x grid caps for axis 0)
+int sweep_candidates(int axis, int nl, int nx, bool dbl, int *out, int max) {
+  int k = 0;
+  if (axis == 0) {
+    for (int i = 0; i < kXCaps && k < max; ++i) out[k++] = i;
+  } else {
+    for (int i = 0; i < kStridedCfgs && k < max; ++i)
+      if (strided_cfg_ok(i, nl, nx, dbl, false)) out[k++] = i;
+  }
+  return k;
+}
+void sweep_config_shape(int axis, int cfg, int *a, int *b, int *c) {
+  if (axis == 0) {
+    *a = 1;
+    *b = 8;
+    *c = xcap(cfg < 0 ? 1 : cfg);
+  } else {
+    const StridedCfg t = strided_cfg(cfg < 0 ? 0 : cfg);
+    *a = t.vw;
+    *b = t.ch;
+    *c = t.w;
+  }
 }
 }  // namespace ibg

@@ -29,7 +29,9 @@ def test_ensemble_equals_members_stepped_alone(prec):
     ens.step(6)
     for g in solo:
         g.step(7)
-    tol = 1e-12 if prec == "fp64" else 1e-5     # atomics reorder the spread sums
+    # atomics (and per-grid autotuned sweep shapes) reorder the FP32 sums; the psi
+    # solve amplifies the difference in p by its conditioning
+    tol = 1e-12 if prec == "fp64" else 1e-4
     for a, b in zip(ens_grids, solo):
         fa, fb = a.fields(), b.fields()
         for k in ("u", "v", "w", "p"):
