@@ -381,6 +381,34 @@ def run_ours(args, rank, world, local):
                            "unit": "cell-updates/s",
                            "one_by_one_ms_per_step": ms_s,
                            "one_by_one_value": cells_e * world / (ms_s * 1e-3)}
+        # stiffness gradient by the discrete adjoint: 96^3 FP32 fields, 7842
+        # markers, one stiffness per connection, 200 steps, checkpoints every
+        # 20 steps (forward, replay of every segment, reverse sweep), against
+        # the same 200 forward steps alone
+        sc_a = I.stiffness_fit_3d()
+        adj = {}
+        for prec_a in ("fp32", "fp64"):
+            ga = ib.Grid(3, sc_a.n, rho=sc_a.rho, mu=sc_a.mu, dt=sc_a.dt, chi=sc_a.chi, precision=prec_a,
+                         kernel=sc_a.kernel, rotate_split=True)
+            ga.add_fiber(sc_a.X, sc_a.edges, sc_a.kappa, sc_a.rest, sc_a.tris)
+            ga.adjoint(20, sc_a.extra["target"], 20)              # warm-up: setup, autotune, graphs
+            barrier()
+            t0 = time.perf_counter()
+            loss_a, _ = ga.adjoint(sc_a.steps, sc_a.extra["target"], 20)
+            barrier()
+            ta = max_over_ranks(time.perf_counter() - t0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ga.step(sc_a.steps)
+            e1.record()
+            barrier()
+            tf = max_over_ranks(e0.elapsed_time(e1)) * 1e-3
+            ga.close()
+            adj[prec_a] = {"s": ta, "forward_s": tf, "ratio_to_forward": ta / tf, "loss": loss_a}
+        out["adjoint"] = {"workload": "d loss / d kappa for 23520 connection stiffnesses, 96^3, 7842 markers, "
+                                      "200 steps, checkpoints every 20 steps",
+                          **{k: {kk: (round(vv, 6) if kk != "loss" else vv) for kk, vv in v.items()}
+                             for k, v in adj.items()}}
         # end to end through the C ABI with host buffers: every step the marker
         # positions come from pinned host memory and go back to it
         ge = make_grid(prec)

@@ -227,6 +227,31 @@ int ib_sweep_config(ib_grid_t g, int axis, int cfg[4]);
 int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels, int *n_kernels);
 const char *ib_kernel_name(int slot);
 
+/* Discrete adjoint of n_steps IB-GM steps with respect to the connection
+ * stiffnesses (no counterpart in the paper, which states no optimisation
+ * problem; the map it differentiates is the step of Sec. 3.4, Steps 1a-3f,
+ * with the connection force of Sec. 4.1, Fig. 3 at zero rest length).
+ *   Advances g by n_steps exactly as ib_step(g, n_steps) does and leaves it
+ *   in that state.  *loss receives sum_k |X_k - X_target_k|^2 over the final
+ *   marker positions and dkappa[e] = d loss / d kappa_e for every connection
+ *   e, in the order the connections were added by ib_add_fiber (all fibers,
+ *   concatenated).  The gradient is the exact transpose of the discrete step
+ *   (weight derivatives of the delta kernel, AB2 histories, the Jacobian of
+ *   the skew-symmetric advection), up to rounding.
+ *   X_target: host, [n_markers][dim] FP64 in the caller's marker order;
+ *   loss: host double; dkappa: host, [n_edges] FP64.
+ *   checkpoint_every >= 1: the state (2 dim + 3 fields, X, U^{n-1}) is kept
+ *   every that many steps; each segment is run forward twice (once to
+ *   checkpoint, once to record u, X, U^{n-1} of its steps) and then backward.
+ *   Device memory: (ceil(n_steps / checkpoint_every) + 1) states, plus
+ *   checkpoint_every * dim fields of tape, plus 4 dim + 4 adjoint fields,
+ *   allocated on entry and freed before return.
+ * Synchronises the grid's stream.  Errors: IB_ERR_ARG (null pointer, n_steps
+ * < 0, checkpoint_every < 1, a non-zero rest length), IB_ERR_OOM (checkpoints
+ * do not fit), IB_ERR_NONFINITE (non-finite final position), IB_ERR_CUDA. */
+int ib_adjoint_run(ib_grid_t g, int n_steps, int checkpoint_every, const double *X_target, double *loss,
+                   double *dkappa);
+
 #ifdef __cplusplus
 }
 #endif

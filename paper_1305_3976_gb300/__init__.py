@@ -27,7 +27,7 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
            "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
-           "ib_sweep_config")
+           "ib_sweep_config", "ib_adjoint_run")
 
 
 class ib_grid_desc(C.Structure):
@@ -77,6 +77,7 @@ def lib():
         L.ib_ensemble_step.argtypes = [vp, C.c_int]
         L.ib_destroy_ensemble.argtypes = [vp]
         L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.ib_adjoint_run.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
         for name in EXPORTS:
@@ -198,6 +199,17 @@ def ib_destroy_grid(g):
     _check(lib().ib_destroy_grid(g), "ib_destroy_grid")
 
 
+def ib_adjoint_run(g, n_steps, checkpoint_every, X_target, n_edges):
+    """Returns (loss, dkappa[n_edges]); X_target is [n_markers][dim] FP64."""
+    T = np.ascontiguousarray(X_target, dtype=np.float64)
+    loss = C.c_double()
+    dk = np.zeros(int(n_edges), dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    _check(lib().ib_adjoint_run(g, int(n_steps), int(checkpoint_every), T.ctypes.data_as(dp), C.byref(loss),
+                                dk.ctypes.data_as(dp)), "ib_adjoint_run")
+    return loss.value, dk
+
+
 def ib_cyclic_solve_lines(precision, dim, n, axis, r, src, dst, stream="current"):
     na = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
     s = _current_stream() if stream == "current" else stream
@@ -267,6 +279,7 @@ class Grid:
         k = {"peskin4": IB_DELTA_PESKIN4, "cos4": IB_DELTA_COS4}.get(kernel, kernel)
         self.h = ib_create_grid(dim, self.n, H, rho, mu, dt, chi, self.precision, k, rotate_split, stream)
         self.n_markers = 0
+        self.n_edges = 0
 
     @property
     def field_shape(self):
@@ -275,6 +288,7 @@ class Grid:
     def add_fiber(self, X, edges, kappa, rest=None, tris=None):
         fid = ib_add_fiber(self.h, X, edges, kappa, rest, tris)
         self.n_markers += np.asarray(X).shape[0]
+        self.n_edges += np.asarray(edges).reshape(-1, 2).shape[0]
         return fid
 
     def set_velocity(self, u):
@@ -316,6 +330,10 @@ class Grid:
     def profile(self, n_steps=1):
         return ib_profile_step(self.h, n_steps)
 
+    def adjoint(self, n_steps, X_target, checkpoint_every=20):
+        """Advance n_steps; return (sum |X - X_target|^2, d loss / d kappa per connection)."""
+        return ib_adjoint_run(self.h, n_steps, checkpoint_every, X_target, self.n_edges)
+
     def sweep_configs(self):
         """Autotuned line-solve configuration per axis: (id, a, b, c)."""
         return [ib_sweep_config(self.h, a) for a in range(self.dim)]
@@ -352,3 +370,36 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+_KAPPA_LOSS = None
+
+
+def kappa_loss(kappa, build, n_steps, X_target, checkpoint_every=20):
+    """Differentiable loss(kappa) = sum_k |X_k^{n_steps} - X_target_k|^2 for
+    torch.autograd: `kappa` is a tensor of connection stiffnesses, `build`
+    maps a numpy copy of it to a fresh Grid with its fibers added.  One call of
+    ib_adjoint_run gives the loss and its gradient; backward returns
+    grad_output * dkappa."""
+    global _KAPPA_LOSS
+    import torch
+
+    if _KAPPA_LOSS is None:
+        class _KappaLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, kap, build_fn, steps, target, ck):
+                g = build_fn(kap.detach().cpu().numpy().astype(np.float64))
+                try:
+                    loss, dk = g.adjoint(steps, target, ck)
+                finally:
+                    g.close()
+                ctx.save_for_backward(torch.from_numpy(dk).to(dtype=kap.dtype, device=kap.device))
+                return kap.new_tensor(loss)
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                (dk,) = ctx.saved_tensors
+                return grad_out * dk, None, None, None, None
+
+        _KAPPA_LOSS = _KappaLoss
+    return _KAPPA_LOSS.apply(kappa, build, n_steps, X_target, checkpoint_every)

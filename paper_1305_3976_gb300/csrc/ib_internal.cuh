@@ -95,6 +95,55 @@ struct MarkerArgs {
   int dim, kernel, first;
 };
 
+// adjoint step (see ib_adjoint.cu)
+template <typename T>
+struct AdjFields {
+  T *ub[3], *pb, *psib, *nbar[3], *divb;  // bars of u, p, psi, N(u^{n-1}), D.u
+  T *q, *rb[3], *vv[3];                   // temporaries
+  long long cells;
+  int n[3];
+  int dim;
+  T ih[3];
+  T chi_mu_half, rho_dt, dt_mu_rho, dt_rho, dt;
+};
+
+template <typename T>
+struct AdjMarkers {
+  const double *X[3];  // X^n (from the tape)
+  const T *Uold[3];    // U^{n-1} (from the tape)
+  T *U[3];             // U^n (recomputed)
+  double *Xh[3];       // X^{n+1/2} (recomputed)
+  T *G[3];             // nodal force (recomputed)
+  T *Gb[3];            // bars of G, X^{n+1/2}, X, U, U^{n-1}
+  double *Xhb[3];
+  double *Xb[3];
+  T *Ub[3];
+  T *Uoldb[3];
+  const int64_t *row;
+  const int32_t *col;
+  const double *kap;
+  const int32_t *cedge;  // connection index of every CSR entry
+  double *dk;            // d(loss)/d kappa, per connection
+  int64_t nm;
+  double dt, H;
+  double inv_h[3];
+  double inv_vol;
+  int n[3];
+  int dim, kernel, first;
+};
+
+template <typename T>
+cudaError_t adjoint_fields_a(const AdjFields<T> &f, cudaStream_t s);
+template <typename T>
+cudaError_t adjoint_fields_b(const AdjFields<T> &f, cudaStream_t s);
+template <typename T>
+cudaError_t adjoint_fields_c(const AdjFields<T> &f, const T *const u[3], int first, cudaStream_t s);
+template <typename T>
+cudaError_t adjoint_markers_pre(const AdjMarkers<T> &am, const T *const u[3], cudaStream_t s);
+template <typename T>
+cudaError_t adjoint_markers_post(const AdjMarkers<T> &am, const T *const rb[3], T dt_rho, const T *const u[3],
+                                 T *const ub[3], cudaStream_t s);
+
 // launchers (return cudaError_t of the launch)
 template <typename T>
 cudaError_t launch_sweep(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s,

@@ -162,6 +162,7 @@ struct ib_grid_s {
   double *acc = nullptr;        // diagnostics accumulators (device)
   double *stage = nullptr;      // [nm][dim] staging buffer for marker I/O
   int32_t *perm = nullptr;      // internal marker k is the caller's marker perm[k]
+  int32_t *cedge = nullptr;     // connection index of every CSR entry
 
   int64_t step = 0;
   bool div_valid = false;
@@ -345,7 +346,7 @@ int upload_markers(ib_grid_s *g) {
     row[E[2 * e + 1] + 1]++;
   }
   for (int64_t a = 0; a < nm; ++a) row[a + 1] += row[a];
-  std::vector<int32_t> col(2 * ne);
+  std::vector<int32_t> col(2 * ne), cedge(2 * ne);
   std::vector<double> kap(2 * ne), rest(2 * ne);
   std::vector<int64_t> fill(row.begin(), row.end() - 1);
   for (int64_t e = 0; e < ne; ++e) {
@@ -353,6 +354,7 @@ int upload_markers(ib_grid_s *g) {
     int64_t pa = fill[a]++, pb = fill[b]++;
     col[pa] = b;
     col[pb] = a;
+    cedge[pa] = cedge[pb] = (int32_t)e;
     kap[pa] = kap[pb] = g->hK[e];
     rest[pa] = rest[pb] = g->hR[e];
   }
@@ -381,6 +383,7 @@ int upload_markers(ib_grid_s *g) {
   const size_t o_acc = take(sizeof(double) * 8);
   const size_t o_stage = take(sizeof(double) * (nm * d + 1));
   const size_t o_perm = take(sizeof(int32_t) * (nm + 1));
+  const size_t o_cedge = take(sizeof(int32_t) * (2 * ne + 1));
   const size_t o_lib = take(sizeof(int32_t) * 2 * d * (nm + 1));
   const size_t o_lsb = take(sizeof(int32_t) * 2 * d * (nm + 1));
   const size_t o_lif = take(es * 4 * 2 * d * (nm + 1));
@@ -412,11 +415,13 @@ int upload_markers(ib_grid_s *g) {
   g->acc = (double *)(base + o_acc);
   g->stage = (double *)(base + o_stage);
   g->perm = (int32_t *)(base + o_perm);
+  g->cedge = (int32_t *)(base + o_cedge);
   IB_CUDA(cudaMemsetAsync(g->mk, 0, off, g->s));
   if (nm) IB_CUDA(cudaMemcpyAsync(g->X[0], soa.data(), sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
   IB_CUDA(cudaMemcpyAsync(g->row, row.data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, g->s));
   if (ne) {
     IB_CUDA(cudaMemcpyAsync(g->col, col.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->cedge, cedge.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->edges, E.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
@@ -533,6 +538,256 @@ int prepare(ib_grid_s *g) {
   const int phases = g->desc.rotate_split ? g->dim : 1;
   for (int ph = 0; ph < phases; ++ph)
     if ((rc = get_graph(g, ph))) return rc;
+  return IB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint driver (kernels in ib_adjoint.cu).
+
+// One forward step of the grid's own path (the body of ib_step's loop).
+int forward_one(ib_grid_s *g) {
+  int rc;
+  if (g->step == 0) {
+    if ((rc = enqueue_step(g, true, 0, nullptr))) return rc;
+  } else {
+    const int phase = g->desc.rotate_split ? (int)(g->step % g->dim) : 0;
+    if ((rc = get_graph(g, phase))) return rc;
+    IB_CUDA(cudaGraphLaunch(g->graph[phase], g->s));
+  }
+  g->step++;
+  return IB_OK;
+}
+
+// device allocations of one adjoint run, freed together
+struct DevPool {
+  std::vector<void *> ptrs;
+  ~DevPool() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  char *get(size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 256) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return (char *)p;
+  }
+};
+
+inline size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Byte sizes of the blocks that make up the state S^n: the fields u, p,
+// psi, Nold, div (the first 2d + 3 slots of the field allocation), the
+// marker positions X (d nm FP64) and U^{n-1} (d nm of the field precision).
+struct StateSizes {
+  size_t fbytes, fields, X, Uold;
+};
+
+StateSizes state_sizes(const ib_grid_s *g) {
+  StateSizes z;
+  z.fbytes = pad256((size_t)g->cells * g->esz);
+  z.fields = z.fbytes * (2 * g->dim + 3);
+  z.X = pad256(sizeof(double) * g->dim * g->nm);
+  z.Uold = pad256(g->esz * g->dim * g->nm);
+  return z;
+}
+
+int copy_state(ib_grid_s *g, char *buf, bool save) {
+  const StateSizes z = state_sizes(g);
+  char *blk[3] = {(char *)g->fields, (char *)g->X[0], (char *)g->Uold[0]};
+  const size_t len[3] = {z.fields, sizeof(double) * g->dim * g->nm, g->esz * g->dim * g->nm};
+  const size_t off[3] = {0, z.fields, z.fields + z.X};
+  for (int i = 0; i < 3; ++i) {
+    if (!len[i]) continue;
+    if (save) IB_CUDA(cudaMemcpyAsync(buf + off[i], blk[i], len[i], cudaMemcpyDeviceToDevice, g->s));
+    else IB_CUDA(cudaMemcpyAsync(blk[i], buf + off[i], len[i], cudaMemcpyDeviceToDevice, g->s));
+  }
+  return IB_OK;
+}
+
+// After a restore: the grid locations of X are stale (recomputed here).
+int relocate(ib_grid_s *g) {
+  g->loc_valid = false;
+  return ensure_loc(g);
+}
+
+template <typename T>
+int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double *loss, double *dkappa) {
+  const int d = g->dim;
+  const int64_t nm = g->nm, ne = g->ne;
+  const StateSizes z = state_sizes(g);
+  const size_t ck_bytes = z.fields + z.X + z.Uold;
+  const size_t tape_fields = z.fbytes * d;  // u^n
+  const size_t tape_bytes = tape_fields + z.X + z.Uold;
+  const int nseg = (n_steps + ck - 1) / ck;
+  const int64_t s0 = g->step;
+  DevPool pool;
+  char *cks = pool.get(ck_bytes * (nseg + 1));  // segment starts + the final state
+  char *tape = pool.get(tape_bytes * (size_t)(n_steps < ck ? (n_steps > 0 ? n_steps : 1) : ck));
+  char *adjf = pool.get(z.fbytes * (4 * d + 4));
+  const size_t mbytes = pad256(sizeof(double) * d * (nm + 1)), tbytes = pad256(sizeof(T) * d * (nm + 1));
+  char *adjm = pool.get(2 * mbytes + 3 * tbytes + pad256(sizeof(double) * (ne + 1)));
+  if (!cks || !tape || !adjf || !adjm)
+    return fail(IB_ERR_OOM, "adjoint: %zu bytes of checkpoints and tape do not fit",
+                ck_bytes * (nseg + 1) + tape_bytes * ck);
+  // forward with checkpoints
+  for (int sg = 0; sg < nseg; ++sg) {
+    int rc = copy_state(g, cks + ck_bytes * sg, true);
+    if (rc) return rc;
+    const int len = std::min(ck, n_steps - sg * ck);
+    for (int j = 0; j < len; ++j)
+      if ((rc = forward_one(g))) return rc;
+  }
+  int rc = copy_state(g, cks + ck_bytes * nseg, true);
+  if (rc) return rc;
+  // loss and its gradient with respect to the final positions (host, FP64)
+  std::vector<double> X(d * nm), Xb(d * nm);
+  std::vector<int32_t> perm(nm);
+  if (nm) {
+    IB_CUDA(cudaMemcpyAsync(X.data(), g->X[0], sizeof(double) * d * nm, cudaMemcpyDeviceToHost, g->s));
+    IB_CUDA(cudaMemcpyAsync(perm.data(), g->perm, sizeof(int32_t) * nm, cudaMemcpyDeviceToHost, g->s));
+  }
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  double L = 0.0;
+  for (int64_t k = 0; k < nm; ++k)
+    for (int a = 0; a < d; ++a) {
+      const double r = X[a * nm + k] - X_target[(int64_t)perm[k] * d + a];
+      if (!isfinite(r)) return fail(IB_ERR_NONFINITE, "adjoint: non-finite marker position");
+      L += r * r;
+      Xb[a * nm + k] = 2.0 * r;
+    }
+  *loss = L;
+  // adjoint state
+  AdjFields<T> f;
+  AdjMarkers<T> am;
+  memset(&f, 0, sizeof(f));
+  memset(&am, 0, sizeof(am));
+  {
+    char *b = adjf;
+    int slot = 0;
+    auto nxt = [&]() { return (T *)(b + z.fbytes * slot++); };
+    for (int a = 0; a < d; ++a) f.ub[a] = nxt();
+    f.pb = nxt();
+    f.psib = nxt();
+    for (int a = 0; a < d; ++a) f.nbar[a] = nxt();
+    f.divb = nxt();
+    f.q = nxt();
+    for (int a = 0; a < d; ++a) f.rb[a] = nxt();
+    for (int a = 0; a < d; ++a) f.vv[a] = nxt();
+    for (int a = d; a < 3; ++a) {
+      f.ub[a] = f.ub[d - 1];
+      f.nbar[a] = f.nbar[d - 1];
+      f.rb[a] = f.rb[d - 1];
+      f.vv[a] = f.vv[d - 1];
+    }
+  }
+  f.cells = g->cells;
+  f.dim = d;
+  for (int a = 0; a < 3; ++a) {
+    f.n[a] = g->n[a];
+    f.ih[a] = (T)(1.0 / g->h[a]);
+  }
+  const ib_grid_desc &D = g->desc;
+  f.chi_mu_half = (T)(0.5 * D.chi * D.mu);
+  f.rho_dt = (T)(D.rho / D.dt);
+  f.dt_mu_rho = (T)(D.dt * D.mu / D.rho);
+  f.dt_rho = (T)(D.dt / D.rho);
+  f.dt = (T)D.dt;
+  double *Xbd = (double *)adjm, *Xhb = (double *)(adjm + mbytes);
+  T *Ub = (T *)(adjm + 2 * mbytes), *Uoldb = (T *)(adjm + 2 * mbytes + tbytes), *Gb = (T *)(adjm + 2 * mbytes + 2 * tbytes);
+  double *dk = (double *)(adjm + 2 * mbytes + 3 * tbytes);
+  IB_CUDA(cudaMemsetAsync(adjf, 0, z.fbytes * (4 * d + 4), g->s));
+  IB_CUDA(cudaMemsetAsync(adjm, 0, 2 * mbytes + 3 * tbytes + pad256(sizeof(double) * (ne + 1)), g->s));
+  if (nm) IB_CUDA(cudaMemcpyAsync(Xbd, Xb.data(), sizeof(double) * d * nm, cudaMemcpyHostToDevice, g->s));
+  for (int a = 0; a < 3; ++a) {
+    const int aa = a < d ? a : d - 1;
+    am.U[a] = (T *)g->U[aa];
+    am.Xh[a] = g->Xh[aa];
+    am.G[a] = (T *)g->G[aa];
+    am.Gb[a] = Gb + aa * nm;
+    am.Xhb[a] = Xhb + aa * nm;
+    am.Xb[a] = Xbd + aa * nm;
+    am.Ub[a] = Ub + aa * nm;
+    am.Uoldb[a] = Uoldb + aa * nm;
+    am.inv_h[a] = 1.0 / g->h[a];
+    am.n[a] = g->n[a];
+  }
+  am.row = g->row;
+  am.col = g->col;
+  am.kap = g->kap;
+  am.cedge = g->cedge;
+  am.dk = dk;
+  am.nm = nm;
+  am.dt = D.dt;
+  am.H = D.H;
+  am.inv_vol = 1.0;
+  for (int a = 0; a < d; ++a) am.inv_vol /= g->h[a];
+  am.dim = d;
+  am.kernel = D.kernel;
+  SweepArgs<T> sa;
+  memset(&sa, 0, sizeof(sa));
+  for (int a = 0; a < 3; ++a) {
+    sa.n[a] = g->n[a];
+    sa.inv_h[a] = (T)(1.0 / g->h[a]);
+  }
+  sa.dim = d;
+  // reverse sweep over the segments
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int len = std::min(ck, n_steps - sg * ck);
+    const int64_t s_seg = s0 + (int64_t)sg * ck;
+    if ((rc = copy_state(g, cks + ck_bytes * sg, false))) return rc;
+    g->step = s_seg;
+    if ((rc = relocate(g))) return rc;
+    for (int j = 0; j < len; ++j) {  // replay, storing u^n, X^n, U^{n-1}
+      char *t = tape + tape_bytes * j;
+      IB_CUDA(cudaMemcpyAsync(t, g->fields, tape_fields, cudaMemcpyDeviceToDevice, g->s));
+      if (nm) {
+        IB_CUDA(cudaMemcpyAsync(t + tape_fields, g->X[0], sizeof(double) * d * nm, cudaMemcpyDeviceToDevice, g->s));
+        IB_CUDA(cudaMemcpyAsync(t + tape_fields + z.X, g->Uold[0], g->esz * d * nm, cudaMemcpyDeviceToDevice, g->s));
+      }
+      if ((rc = forward_one(g))) return rc;
+    }
+    for (int j = len - 1; j >= 0; --j) {  // adjoint steps, last first
+      char *t = tape + tape_bytes * j;
+      const int first = s_seg + j == 0;
+      const T *u[3];
+      for (int a = 0; a < 3; ++a) u[a] = (const T *)(t + z.fbytes * (a < d ? a : d - 1));
+      // Steps 3e-3f: q = A^{-1}(psi_bar + p_bar), then the bars of D.u' and u'
+      IB_CUDA(adjoint_fields_a<T>(f, g->s));
+      sa.f[0] = sa.f[1] = sa.f[2] = f.q;
+      for (int ax = 0; ax < d; ++ax) {
+        sa.co = coef_of<T>(g->coef[1][ax]);
+        IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, 1, sa, g->s, g->tune[ax]));
+      }
+      IB_CUDA(adjoint_fields_b<T>(f, g->s));
+      // Steps 3c-3d: R_bar = M^{-1} u'_bar
+      for (int a = 0; a < 3; ++a) sa.f[a] = f.rb[a];
+      for (int ax = 0; ax < d; ++ax) {
+        sa.co = coef_of<T>(g->coef[0][ax]);
+        IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, g->tune[ax]));
+      }
+      // Steps 3a-3b
+      IB_CUDA(adjoint_fields_c<T>(f, u, first, g->s));
+      // Steps 1a-2b
+      if (nm) {
+        for (int a = 0; a < 3; ++a) {
+          const int aa = a < d ? a : d - 1;
+          am.X[a] = (const double *)(t + tape_fields) + aa * nm;
+          am.Uold[a] = (const T *)(t + tape_fields + z.X) + aa * nm;
+        }
+        am.first = first;
+        IB_CUDA(adjoint_markers_pre<T>(am, u, g->s));
+        IB_CUDA(launch_force<T>(marker_args(g, first), g->s));
+        IB_CUDA(cudaMemsetAsync(Xhb, 0, sizeof(double) * d * nm, g->s));
+        const T *rbc[3] = {f.rb[0], f.rb[1], f.rb[2]};
+        IB_CUDA(adjoint_markers_post<T>(am, rbc, f.dt_rho, u, f.ub, g->s));
+      }
+    }
+  }
+  // leave the grid in the final state, as ib_step would
+  if ((rc = copy_state(g, cks + ck_bytes * nseg, false))) return rc;
+  g->step = s0 + n_steps;
+  if ((rc = relocate(g))) return rc;
+  if (ne) IB_CUDA(cudaMemcpyAsync(dkappa, dk, sizeof(double) * ne, cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));
   return IB_OK;
 }
 
@@ -901,6 +1156,22 @@ int ib_split_solve(int precision, int dim, const int n[3], const double r[3], co
     if (rc) return rc;
   }
   return IB_OK;
+}
+
+int ib_adjoint_run(ib_grid_t g, int n_steps, int checkpoint_every, const double *X_target, double *loss,
+                   double *dkappa) {
+  if (!g || !loss || n_steps < 0 || checkpoint_every < 1) return fail(IB_ERR_ARG, "bad argument");
+  if (g->nm && !X_target) return fail(IB_ERR_ARG, "null X_target");
+  if (g->ne && !dkappa) return fail(IB_ERR_ARG, "null dkappa");
+  for (double r : g->hR)
+    if (r != 0.0) return fail(IB_ERR_ARG, "the adjoint needs every rest length to be 0");
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((rc = prepare(g))) return rc;
+  rc = g->prec == IB_FP32 ? adjoint_t<float>(g, n_steps, checkpoint_every, X_target, loss, dkappa)
+                          : adjoint_t<double>(g, n_steps, checkpoint_every, X_target, loss, dkappa);
+  if (rc) return rc;
+  return leave(g);
 }
 
 }  // extern "C"

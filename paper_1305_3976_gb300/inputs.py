@@ -323,3 +323,38 @@ def random_ellipsoids_3d(n=512, count=8, nu=80, seed=DEFAULT_SEED, mu=0.01, dt=3
                  kappa=np.full(Eall.shape[0], sigma), rest=np.zeros(Eall.shape[0]),
                  tris=np.concatenate(Ts).astype(np.int32),
                  name=f"3D {count} random ellipsoids {n}^3, nu={nu}")
+
+
+def stiffness_fit_3d(n=96, nu=28, seed=DEFAULT_SEED, axes=(0.2, 0.25, 0.3), sigma_range=(0.5, 2.0), rho=1.0,
+                     mu=0.05, dt=5e-4, steps=200, kernel="peskin4") -> Scene:
+    """Stiffness-gradient problem: the ellipsoidal membrane of ellipsoid_3d
+    (icosahedral nu mesh, 10 nu^2 + 2 markers; nu = 28 gives 7842 markers
+    and 23520 connections) with one stiffness per connection drawn uniform in
+    sigma_range, zero rest lengths.  extra["target"] holds the same mesh on
+    the sphere of equal volume (radius (a b c)^(1/3), same centre) plus
+    Gaussian jitter of standard deviation h / 10; the loss is
+    sum_k |X_k - target_k|^2 after `steps` steps."""
+    g = rng(seed)
+    X, E, _, rest, T = ellipsoid_membrane(nu, axes, (0.5, 0.5, 0.5))
+    kappa = g.uniform(*sigma_range, size=E.shape[0])
+    V, _, _ = icosphere(nu)
+    r = float(np.prod(axes)) ** (1.0 / 3.0)
+    target = V * r + 0.5 + g.normal(0.0, 0.1 / n, size=V.shape)
+    return Scene(dim=3, n=(n, n, n), rho=rho, mu=mu, dt=dt, steps=steps, X=X, edges=E, kappa=kappa, rest=rest,
+                 tris=T, kernel=kernel, name=f"stiffness fit {n}^3, nu={nu} ({X.shape[0]} markers)",
+                 extra={"target": target})
+
+
+def stiffness_fit_2d(n=32, ns=64, seed=DEFAULT_SEED, r1=0.2, r2=0.25, sigma_range=(0.5, 2.0), rho=1.0, mu=0.1,
+                     dt=1e-3, steps=20, kernel="cos4") -> Scene:
+    """2D counterpart of stiffness_fit_3d: a closed elliptical fiber of ns
+    points with kappa_e = sigma_e ns, sigma_e uniform in sigma_range, zero
+    rest lengths; target: the circle of equal area plus h / 10 jitter."""
+    g = rng(seed)
+    X = ellipse_points(ns, r1, r2)
+    edges, _, rest = closed_fiber_connections(ns, 1.0, 0.0)
+    kappa = g.uniform(*sigma_range, size=ns) * ns
+    r = float(np.sqrt(r1 * r2))
+    target = ellipse_points(ns, r, r) + g.normal(0.0, 0.1 / n, size=X.shape)
+    return Scene(dim=2, n=(n, n), rho=rho, mu=mu, dt=dt, steps=steps, X=X, edges=edges, kappa=kappa, rest=rest,
+                 kernel=kernel, name=f"2D stiffness fit {n}^2, {ns} markers", extra={"target": target})
