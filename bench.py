@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--nu", type=int, default=64)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, line-solve, e2e and CPU legs")
+    ap.add_argument("--sweep-config", default=None,
+                    help="comma-separated line-solve configuration ids per axis (as printed under "
+                         "sweep_configs) to use instead of autotuning, e.g. to profile a run's choice")
     return ap.parse_args()
 
 
@@ -236,6 +239,8 @@ def run_ours(args, rank, world, local):
         g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=prec, kernel=sc.kernel,
                     rotate_split=True)
         g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+        if args.sweep_config and prec == args.precision:
+            g.fix_sweep_configs([int(x) for x in args.sweep_config.split(",")])
         return g
 
     def timed_steps(g, K, W):

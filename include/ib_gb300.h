@@ -219,6 +219,13 @@ int ib_split_solve_noalloc(int precision, int dim, const int n[3], const double 
  * CTAs per SM.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
 int ib_sweep_config(ib_grid_t g, int axis, int cfg[4]);
 
+/* Use line-solve configuration `id` (an id that ib_sweep_config reported for
+ * a grid of the same size and precision) for `axis` instead of timing the
+ * candidates, e.g. to reproduce a run's choice under a profiler, where timings
+ * are distorted.  Only before the first step.  Errors: IB_ERR_ARG (axis, or
+ * id not a candidate for this grid), IB_ERR_STATE (grid already stepped). */
+int ib_fix_sweep_config(ib_grid_t g, int axis, int id);
+
 /* Run n_steps steps with every kernel launched on its own and timed by CUDA
  * events on the grid's stream; kernel_ms[i] receives the total milliseconds
  * of kernel slot i (at most max_kernels slots, *n_kernels gets the count) and

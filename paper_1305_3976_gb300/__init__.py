@@ -27,7 +27,7 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
            "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
-           "ib_sweep_config", "ib_adjoint_run")
+           "ib_sweep_config", "ib_fix_sweep_config", "ib_adjoint_run")
 
 
 class ib_grid_desc(C.Structure):
@@ -77,6 +77,7 @@ def lib():
         L.ib_ensemble_step.argtypes = [vp, C.c_int]
         L.ib_destroy_ensemble.argtypes = [vp]
         L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.ib_fix_sweep_config.argtypes = [vp, C.c_int, C.c_int]
         L.ib_adjoint_run.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
@@ -240,6 +241,10 @@ def ib_sweep_config(g, axis):
     return tuple(cfg)
 
 
+def ib_fix_sweep_config(g, axis, cfg_id):
+    _check(lib().ib_fix_sweep_config(g, int(axis), int(cfg_id)), "ib_fix_sweep_config")
+
+
 def ib_profile_step(g, n_steps):
     ms = (C.c_float * 16)()
     nk = C.c_int()
@@ -337,6 +342,11 @@ class Grid:
     def sweep_configs(self):
         """Autotuned line-solve configuration per axis: (id, a, b, c)."""
         return [ib_sweep_config(self.h, a) for a in range(self.dim)]
+
+    def fix_sweep_configs(self, ids):
+        """Use these configuration ids (one per axis) instead of timing candidates."""
+        for a, i in enumerate(ids):
+            ib_fix_sweep_config(self.h, a, i)
 
     def close(self):
         if self.h:

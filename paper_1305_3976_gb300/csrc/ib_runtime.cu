@@ -169,6 +169,7 @@ struct ib_grid_s {
   bool loc_valid = false;       // locI holds the grid locations of the current X
   bool tuned = false;
   int tune[3] = {-1, -1, -1};   // sweep configuration per axis (autotuned)
+  bool fixed[3] = {false, false, false};  // set by ib_fix_sweep_config: not timed
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -491,6 +492,7 @@ int autotune_t(ib_grid_s *g) {
   IB_CUDA(cudaEventCreate(&e1));
   int rc = IB_OK;
   for (int ax = 0; ax < d && !rc; ++ax) {
+    if (g->fixed[ax]) continue;
     sa.co = coef_of<T>(g->coef[0][ax]);
     int cand[16];
     const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 16);
@@ -1012,6 +1014,19 @@ int ib_sweep_config(ib_grid_t g, int axis, int *cfg) {
   const int id = g->tune[axis];
   sweep_config_shape(axis, id, &cfg[1], &cfg[2], &cfg[3]);
   cfg[0] = id;
+  return IB_OK;
+}
+
+int ib_fix_sweep_config(ib_grid_t g, int axis, int id) {
+  if (!g || axis < 0 || axis >= g->dim) return fail(IB_ERR_ARG, "bad argument");
+  if (g->tuned || g->step != 0) return fail(IB_ERR_STATE, "sweep configurations are fixed before the first step");
+  int cand[16];
+  const int nc = sweep_candidates(axis, g->n[axis], g->n[0], g->prec == IB_FP64, cand, 16);
+  bool ok = false;
+  for (int i = 0; i < nc; ++i) ok = ok || cand[i] == id;
+  if (!ok) return fail(IB_ERR_ARG, "configuration %d is not a candidate for axis %d of this grid", id, axis);
+  g->tune[axis] = id;
+  g->fixed[axis] = true;
   return IB_OK;
 }
 

@@ -161,3 +161,23 @@ def test_state_errors():
     assert ex.value.code == ib.IB_ERR_NONFINITE
     g.close()
     g2.close()
+
+
+def test_fixed_sweep_configuration_replaces_the_autotuner():
+    sc = small_ellipsoid(n=32, nu=8)
+    _, g0 = make_pair(sc, "fp32")
+    g0.step(2)
+    ids = [c[0] for c in g0.sweep_configs()]
+    _, g1 = make_pair(sc, "fp32")
+    with pytest.raises(ib.IBError) as ex:
+        ib.ib_fix_sweep_config(g1.h, 1, 99)
+    assert ex.value.code == ib.IB_ERR_ARG
+    g1.fix_sweep_configs(ids)
+    g1.step(2)
+    assert [c[0] for c in g1.sweep_configs()] == ids
+    assert rel(g1.velocity(), g0.velocity()) < 1e-5
+    with pytest.raises(ib.IBError) as ex:
+        g1.fix_sweep_configs(ids)
+    assert ex.value.code == ib.IB_ERR_STATE
+    g0.close()
+    g1.close()
