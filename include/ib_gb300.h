@@ -45,6 +45,7 @@ enum {
 
 enum { IB_FP32 = 0, IB_FP64 = 1 };                 /* field precision          */
 enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };  /* 1D kernel phi(r)         */
+enum { IB_GM2 = 0, IB_GM1 = 1 };                   /* pseudo-compressibility   */
 
 /* field selection bits for ib_read_fields */
 enum {
@@ -69,7 +70,13 @@ typedef struct ib_grid_s *ib_grid_t;
  *                (phi = (1 + cos(pi r / 2)) / 4 on |r| < 2).
  *   rotate_split 1: step n applies the direction-split factors in the order
  *                cyclically shifted by n mod dim (Sec. 4.1); 0: x, y(, z).
- *   stream       cudaStream_t the grid works on (NULL: default stream).      */
+ *   stream       cudaStream_t the grid works on (NULL: default stream).
+ *   scheme       IB_GM2 (0): the second-order Guermond-Minev variant the paper
+ *                uses (Sec. 3.1 eqs. PerturbNSE2-PerturbCorrection2; Sec. 3.4
+ *                Steps 3a, 3e, 3f).  IB_GM1 (1): the first-order variant of
+ *                Sec. 3.1, (eps/rho) A p + D.u = 0 with eps = dt: Step 3a
+ *                uses p* = p^{n-1/2}, the solve of Step 3e gives p^{n+1/2}
+ *                itself, chi is not used.                                   */
 typedef struct {
   int dim;
   int n[3];
@@ -78,6 +85,7 @@ typedef struct {
   int kernel;
   int rotate_split;
   void *stream;
+  int scheme;
 } ib_grid_desc;
 
 /* FP64 diagnostics (Sec. 5.1 volume conservation; discrete l2 norms of

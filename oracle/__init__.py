@@ -56,7 +56,7 @@ def lib():
 class Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("H", C.c_double), ("rho", C.c_double),
                 ("mu", C.c_double), ("dt", C.c_double), ("chi", C.c_double), ("kernel", C.c_int),
-                ("rotate", C.c_int), ("schur_P", C.c_int)]
+                ("rotate", C.c_int), ("schur_P", C.c_int), ("scheme", C.c_int)]
 
 
 class State(C.Structure):
@@ -71,9 +71,14 @@ class State(C.Structure):
 KERNELS = {"peskin4": 0, "cos4": 1}
 
 
+SCHEMES = {"gm2": 0, "gm1": 1}
+
+
 def params(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, kernel="peskin4", rotate=False,
-           schur_P=1):
-    """Problem parameters; n is an int (same N on every axis) or a sequence."""
+           schur_P=1, scheme="gm2"):
+    """Problem parameters; n is an int (same N on every axis) or a sequence.
+    scheme: "gm2" (the paper's second-order GM variant) or "gm1" (its
+    first-order variant, Sec. 3.1)."""
     if np.isscalar(n):
         n = [int(n)] * dim
     n = list(n) + [1] * (3 - len(n))
@@ -86,6 +91,7 @@ def params(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, kernel="peskin4", r
     P.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     P.rotate = int(bool(rotate))
     P.schur_P = int(schur_P)
+    P.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     return P
 
 

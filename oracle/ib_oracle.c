@@ -43,6 +43,10 @@ typedef struct {
   int kernel;    /* 0: 4-point kernel of eq. (discretedelta); 1: cosine      */
   int rotate;    /* 1: rotate the direction-split order with the step index */
   int schur_P;   /* number of blocks in the Schur line solve (>= 1)          */
+  int scheme;    /* 0: the second-order GM variant of Sec. 3.4 (eqs.
+                    PerturbNSE2-PerturbCorrection2); 1: the first-order
+                    variant of Sec. 3.1, (eps/rho) A p + div u = 0 with
+                    eps = dt (eqs. PerturbNSE-PerturbIncompressible)         */
 } ibo_params;
 
 typedef struct {
@@ -578,8 +582,10 @@ int ibo_step(const ibo_params *P, ibo_state *S) {
   ibo_force_edges(d, P->H, Xh, nm, S->edges, S->kappa, S->rest, S->ne, G);
   /* Step 2b */
   ibo_spread(P, Xh, G, nm, f);
-  /* Step 3a (p* = 0 when n = 0) */
-  for (long i = 0; i < cells; ++i) pstar[i] = (n == 0) ? 0.0 : S->p[i] + S->psi[i];
+  /* Step 3a (p* = 0 when n = 0).  First-order variant: the momentum step
+   * sees the latest pressure p^{n-1/2} itself. */
+  for (long i = 0; i < cells; ++i)
+    pstar[i] = (n == 0) ? 0.0 : (P->scheme == 1 ? S->p[i] : S->p[i] + S->psi[i]);
   /* Step 3b: rho((u* - u^n)/dt + N^{n+1/2}) = mu L u^n - G p* + f */
   ibo_advection(P, S->u, Nn);
   ibo_gradient(P, pstar, gp);
@@ -619,10 +625,16 @@ int ibo_step(const ibo_params *P, ibo_state *S) {
     double h = h_of(P, ax);
     rc |= ibo_solve_lines(P, ax, 1.0 / (h * h), S->psi);
   }
-  /* Step 3f: p^{n+1/2} = p^{n-1/2} + psi - chi mu D.(1/2 (u^{n+1} + u^n)) */
-  for (long i = 0; i < (long)d * cells; ++i) avg[i] = 0.5 * (cur[i] + S->u[i]);
-  ibo_divergence(P, avg, div);
-  for (long i = 0; i < cells; ++i) S->p[i] = S->p[i] + S->psi[i] - P->chi * mu * div[i];
+  /* Step 3f: p^{n+1/2} = p^{n-1/2} + psi - chi mu D.(1/2 (u^{n+1} + u^n)).
+   * First-order variant: the solve above is the pressure itself,
+   * (dt/rho) A p^{n+1/2} = -D.u^{n+1}. */
+  if (P->scheme == 1) {
+    for (long i = 0; i < cells; ++i) S->p[i] = S->psi[i];
+  } else {
+    for (long i = 0; i < (long)d * cells; ++i) avg[i] = 0.5 * (cur[i] + S->u[i]);
+    ibo_divergence(P, avg, div);
+    for (long i = 0; i < cells; ++i) S->p[i] = S->p[i] + S->psi[i] - P->chi * mu * div[i];
+  }
 
   /* roll the state forward */
   memcpy(S->u, cur, sizeof(double) * d * cells);

@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 IB_OK, IB_ERR_ARG, IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_NONFINITE, IB_ERR_TIMEOUT, IB_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 IB_FP32, IB_FP64 = 0, 1
 IB_DELTA_PESKIN4, IB_DELTA_COS4 = 0, 1
+IB_GM2, IB_GM1 = 0, 1
 IB_FIELD_U, IB_FIELD_V, IB_FIELD_W, IB_FIELD_P, IB_FIELD_PSI, IB_FIELD_DIV = 1, 2, 4, 8, 16, 32
 FIELD_BITS = ("u", "v", "w", "p", "psi", "div")
 
@@ -33,7 +34,7 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
 class ib_grid_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("H", C.c_double), ("rho", C.c_double),
                 ("mu", C.c_double), ("dt", C.c_double), ("chi", C.c_double), ("precision", C.c_int),
-                ("kernel", C.c_int), ("rotate_split", C.c_int), ("stream", C.c_void_p)]
+                ("kernel", C.c_int), ("rotate_split", C.c_int), ("stream", C.c_void_p), ("scheme", C.c_int)]
 
 
 class ib_diag(C.Structure):
@@ -131,7 +132,7 @@ def _current_stream():
 
 
 def ib_create_grid(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision=IB_FP32,
-                   kernel=IB_DELTA_PESKIN4, rotate_split=1, stream="current"):
+                   kernel=IB_DELTA_PESKIN4, rotate_split=1, stream="current", scheme=IB_GM2):
     d = ib_grid_desc()
     d.dim = dim
     n = [int(n)] * dim if np.isscalar(n) else list(n)
@@ -140,6 +141,7 @@ def ib_create_grid(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision=I
     d.H, d.rho, d.mu, d.dt, d.chi = H, rho, mu, dt, chi
     d.precision, d.kernel, d.rotate_split = precision, kernel, int(rotate_split)
     d.stream = _current_stream() if stream == "current" else stream
+    d.scheme = scheme
     h = C.c_void_p()
     _check(lib().ib_create_grid(C.byref(d), C.byref(h)), "ib_create_grid")
     return h
@@ -276,13 +278,14 @@ class Grid:
     """An ib_grid_t with numpy/torch conveniences (argument marshalling only)."""
 
     def __init__(self, dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision="fp32",
-                 kernel="peskin4", rotate_split=True, stream="current"):
+                 kernel="peskin4", rotate_split=True, stream="current", scheme="gm2"):
         self.dim = dim
         self.n = [int(n)] * dim if np.isscalar(n) else list(n)[:dim]
         self.precision = IB_FP32 if precision in ("fp32", IB_FP32) else IB_FP64
         self.dtype = np.float32 if self.precision == IB_FP32 else np.float64
         k = {"peskin4": IB_DELTA_PESKIN4, "cos4": IB_DELTA_COS4}.get(kernel, kernel)
-        self.h = ib_create_grid(dim, self.n, H, rho, mu, dt, chi, self.precision, k, rotate_split, stream)
+        s = {"gm2": IB_GM2, "gm1": IB_GM1}.get(scheme, scheme)
+        self.h = ib_create_grid(dim, self.n, H, rho, mu, dt, chi, self.precision, k, rotate_split, stream, s)
         self.n_markers = 0
         self.n_edges = 0
 

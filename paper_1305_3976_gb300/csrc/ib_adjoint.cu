@@ -5,6 +5,7 @@
 // adjoint (bar) of S^{n+1}, the kernels below produce the bar of S^n and add
 // d(loss)/d kappa.  Structure, in reverse order of the forward step:
 //   3f/3e  p' = p - chi mu/2 (D.u' + D.u) + psi',  psi' = A^{-1}(-rho/dt D.u')
+//          (first-order variant of Sec. 3.1: p' = psi', and p* = p below)
 //          with A = prod (I - D_aa) symmetric, and D^T = -G;
 //   3c-3d  u' = u + M^{-1} R, M = prod (I - a D_aa) symmetric;
 //   3a-3b  R = dt [(mu L u - G p* + f)/rho - (c1 N(u) + c2 N(u^{n-1}))],
@@ -90,12 +91,15 @@ __global__ void k_adj_q(const T *psib, const T *pb, T *q, long long cells) {
 
 // A3: with q = A^{-1}(psi_bar + p_bar):  D.u' bar  = divb - chi mu/2 pb - rho/dt q
 // (stored in q); the bar of D.u^n is -chi mu/2 pb
+// (first-order variant: chi = 0 and p' = psi', so the bar of p^n keeps
+// p_keep = 0 of pb)
 template <typename T>
-__global__ void k_adj_div(T *q, T *divb, const T *pb, T chi_mu_half, T rho_dt, long long cells) {
+__global__ void k_adj_div(T *q, T *divb, T *pb, T chi_mu_half, T rho_dt, T p_keep, long long cells) {
   for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (long long)gridDim.x * blockDim.x) {
     const T p = pb[o];
     q[o] = divb[o] - chi_mu_half * p - rho_dt * q[o];
     divb[o] = -chi_mu_half * p;
+    pb[o] = p_keep * p;
   }
 }
 
@@ -123,13 +127,13 @@ __global__ void k_adj_grad(T *ub0, T *ub1, T *ub2, T *rb0, T *rb1, T *rb2, const
 }
 
 // A5 (after the momentum solves Rb = M^{-1} u'bar):
-//   ub += dt mu/rho L Rb;  (n > 0) pb += dt/rho D.Rb, psib = dt/rho D.Rb;
+//   ub += dt mu/rho L Rb;  (n > 0) pb += dt/rho D.Rb, psib = psi_w dt/rho D.Rb;
 //   V = -dt c1 Rb + Nb (the bar of N(u^n), scattered by k_adj_adv);
 //   Nb = -c2 (-dt) Rb ... = dt/2 Rb (n > 0) or 0
 template <typename T, int DIM>
 __global__ void k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, const T *rb2, T *nb0, T *nb1, T *nb2,
                           T *v0, T *v1, T *v2, T *pb, T *psib, int nx, int ny, int nz, T ihx, T ihy, T ihz,
-                          T dt_mu_rho, T dt_rho, T dt, int first) {
+                          T dt_mu_rho, T dt_rho, T dt, T psi_w, int first) {
   const long long cells = (long long)nx * ny * nz;
   T *ub[3] = {ub0, ub1, ub2}, *nb[3] = {nb0, nb1, nb2}, *vv[3] = {v0, v1, v2};
   const T *rb[3] = {rb0, rb1, rb2};
@@ -157,7 +161,7 @@ __global__ void k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, co
     }
     if (!first) {
       pb[o] += dt_rho * divR;
-      psib[o] = dt_rho * divR;
+      psib[o] = psi_w * dt_rho * divR;
     } else {
       psib[o] = T(0);
     }
@@ -382,7 +386,7 @@ cudaError_t adjoint_fields_a(const AdjFields<T> &f, cudaStream_t s) {
 
 template <typename T>
 cudaError_t adjoint_fields_b(const AdjFields<T> &f, cudaStream_t s) {
-  k_adj_div<T><<<nb(f.cells), 256, 0, s>>>(f.q, f.divb, f.pb, f.chi_mu_half, f.rho_dt, f.cells);
+  k_adj_div<T><<<nb(f.cells), 256, 0, s>>>(f.q, f.divb, f.pb, f.chi_mu_half, f.rho_dt, f.p_keep, f.cells);
   if (f.dim == 2)
     k_adj_grad<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.q, f.n[0],
                                                  f.n[1], 1, f.ih[0], f.ih[1], T(0));
@@ -397,14 +401,15 @@ cudaError_t adjoint_fields_c(const AdjFields<T> &f, const T *const u[3], int fir
   if (f.dim == 2) {
     k_adj_rhs<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.nbar[0],
                                                 f.nbar[1], f.nbar[1], f.vv[0], f.vv[1], f.vv[1], f.pb, f.psib, f.n[0],
-                                                f.n[1], 1, f.ih[0], f.ih[1], T(0), f.dt_mu_rho, f.dt_rho, f.dt, first);
+                                                f.n[1], 1, f.ih[0], f.ih[1], T(0), f.dt_mu_rho, f.dt_rho, f.dt, f.psi_w,
+                                                first);
     k_adj_adv<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], u[0], u[1], u[1], f.vv[0], f.vv[1],
                                                 f.vv[1], f.n[0], f.n[1], 1, f.ih[0], f.ih[1], T(0));
   } else {
     k_adj_rhs<T, 3><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[2], f.rb[0], f.rb[1], f.rb[2], f.nbar[0],
                                                 f.nbar[1], f.nbar[2], f.vv[0], f.vv[1], f.vv[2], f.pb, f.psib, f.n[0],
                                                 f.n[1], f.n[2], f.ih[0], f.ih[1], f.ih[2], f.dt_mu_rho, f.dt_rho,
-                                                f.dt, first);
+                                                f.dt, f.psi_w, first);
     k_adj_adv<T, 3><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[2], u[0], u[1], u[2], f.vv[0], f.vv[1],
                                                 f.vv[2], f.n[0], f.n[1], f.n[2], f.ih[0], f.ih[1], f.ih[2]);
   }

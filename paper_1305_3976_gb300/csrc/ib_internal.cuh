@@ -53,6 +53,7 @@ struct SweepArgs {
   T *div;         // PRO_DIV: D.u^n in, D.u^{n+1} out
   T pro_scale;    // PRO_DIV: -rho / dt
   T chi_mu_half;  // PRO_DIV: chi mu / 2
+  T p_keep;       // PRO_DIV: weight of p^{n-1/2} in p^{n+1/2} (1; 0 in the first-order variant)
   T inv_h[3];
   int n[3];
   int dim;
@@ -62,7 +63,7 @@ struct SweepArgs {
 template <typename T>
 struct RhsArgs {
   const T *u[3];
-  const T *p, *psi;
+  const T *p, *psi;  // p* = p + psi (psi null: p* = p, the first-order variant)
   T *Nold[3];     // in: N(u^{n-1}); out: N(u^n)
   T *scr[3];      // in: spread force f; out: R = u* - u^n
   T inv_h[3], inv_h2[3];
@@ -105,6 +106,8 @@ struct AdjFields {
   int dim;
   T ih[3];
   T chi_mu_half, rho_dt, dt_mu_rho, dt_rho, dt;
+  T p_keep;  // weight of p^{n-1/2} in p^{n+1/2}
+  T psi_w;   // weight of psi^{n-1/2} in p*
 };
 
 template <typename T>

@@ -51,12 +51,12 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
     for (int c = 0; c < DIM; ++c)
 #pragma unroll
       for (int ax = 0; ax < DIM; ++ax) ux[c][ax] = ax == c ? T(0) : a.u[ax][o + dp[ax] + dm[c]];
-    const T p0 = a.first ? T(0) : a.p[o] + a.psi[o];
+    const T p0 = a.first ? T(0) : a.p[o] + (a.psi ? a.psi[o] : T(0));
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       f[c] = a.scr[c][o];
       nold[c] = a.first ? T(0) : a.Nold[c][o];
-      pm[c] = a.first ? T(0) : a.p[o + dm[c]] + a.psi[o + dm[c]];
+      pm[c] = a.first ? T(0) : a.p[o + dm[c]] + (a.psi ? a.psi[o + dm[c]] : T(0));
     }
     T R[DIM], Nn[DIM];
 #pragma unroll
@@ -148,12 +148,14 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
     T t0[4], t1[4];
     ld4(a.Nold[C] + ro + x0, nold);
     get4(a.p, ro, x0, nx, 0, t0);
-    get4(a.psi, ro, x0, nx, 0, t1);
+    if (a.psi) get4(a.psi, ro, x0, nx, 0, t1);
+    else t1[0] = t1[1] = t1[2] = t1[3] = T(0);
 #pragma unroll
     for (int e = 0; e < 4; ++e) P0[e] = t0[e] + t1[e];
     const int rm = C == 0 ? ro : (C == 1 ? R(ym, z) : R(y, zm));
     get4(a.p, rm, x0, nx, C == 0 ? -1 : 0, t0);
-    get4(a.psi, rm, x0, nx, C == 0 ? -1 : 0, t1);
+    if (a.psi) get4(a.psi, rm, x0, nx, C == 0 ? -1 : 0, t1);
+    else t1[0] = t1[1] = t1[2] = t1[3] = T(0);
 #pragma unroll
     for (int e = 0; e < 4; ++e) Pm[e] = t0[e] + t1[e];
   } else {

@@ -50,6 +50,13 @@ __device__ __forceinline__ T div_at(const SweepArgs<T> &a, int i, int j, int k) 
   return d;
 }
 
+// p^{n-1/2} as it enters p^{n+1/2}: itself (Step 3f), or nothing in the
+// first-order variant (Sec. 3.1), whose solve gives the pressure directly
+template <typename T>
+__device__ __forceinline__ T kept_p(const SweepArgs<T> &a, T p) {
+  return a.p_keep != T(0) ? a.p_keep * p : T(0);
+}
+
 // Prologue of the first psi sweep (Step 3e right-hand side -rho/dt D.u^{n+1},
 // and the -chi mu D.(u^{n+1} + u^n)/2 part of Step 3f): returns the
 // right-hand side and the new div and p values, which the caller stores after
@@ -58,7 +65,7 @@ template <typename T>
 __device__ __forceinline__ T div_prologue(const SweepArgs<T> &a, long long o, int i, int j, int k, T &dnew,
                                           T &pnew) {
   dnew = div_at(a, i, j, k);
-  pnew = a.p[o] - a.chi_mu_half * (dnew + a.div[o]);
+  pnew = kept_p(a, a.p[o]) - a.chi_mu_half * (dnew + a.div[o]);
   return a.pro_scale * dnew;
 }
 
@@ -309,7 +316,7 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
         d += (vj1[e] - vj[e]) * a.inv_h[1];
         if (a.dim == 3) d += (wk1[e] - w4[e]) * a.inv_h[2];
         dn[PRO == PRO_DIV ? r : 0][e] = d;
-        pn[PRO == PRO_DIV ? r : 0][e] = p4[e] - a.chi_mu_half * (d + d4[e]);
+        pn[PRO == PRO_DIV ? r : 0][e] = kept_p(a, p4[e]) - a.chi_mu_half * (d + d4[e]);
         v[r][e] = i0 < nx ? a.pro_scale * d : T(0);
       }
     } else {
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
           T d = (up - u0[c]) * a.inv_h[0];
           d += (v1[c] - v0[c]) * a.inv_h[1];
           if (a.dim == 3) d += (w1[c] - w0[c]) * a.inv_h[2];
-          pn[PRO == PRO_DIV ? e : 0][c] = pv[c] - a.chi_mu_half * (d + dv[c]);
+          pn[PRO == PRO_DIV ? e : 0][c] = kept_p(a, pv[c]) - a.chi_mu_half * (d + dv[c]);
           v[e][c] = a.pro_scale * d;
         }
       }

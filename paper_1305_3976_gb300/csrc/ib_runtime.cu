@@ -243,8 +243,9 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     ra.inv_h2[a] = (T)(1.0 / (g->h[a] * g->h[a]));
     ra.n[a] = g->n[a];
   }
+  const bool gm1 = g->desc.scheme == IB_GM1;
   ra.p = (const T *)g->p;
-  ra.psi = (const T *)g->psi;
+  ra.psi = gm1 ? nullptr : (const T *)g->psi;
   ra.mu = (T)g->desc.mu;
   ra.inv_rho = (T)(1.0 / g->desc.rho);
   ra.dt = (T)g->desc.dt;
@@ -264,7 +265,8 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   sa.p = (T *)g->p;
   sa.div = (T *)g->div;
   sa.pro_scale = (T)(-g->desc.rho / g->desc.dt);
-  sa.chi_mu_half = (T)(0.5 * g->desc.chi * g->desc.mu);
+  sa.chi_mu_half = gm1 ? T(0) : (T)(0.5 * g->desc.chi * g->desc.mu);
+  sa.p_keep = gm1 ? T(0) : T(1);
   sa.dim = d;
   for (int st = 0; st < d; ++st) {
     const int ax = order[st];
@@ -688,7 +690,10 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
     f.ih[a] = (T)(1.0 / g->h[a]);
   }
   const ib_grid_desc &D = g->desc;
-  f.chi_mu_half = (T)(0.5 * D.chi * D.mu);
+  const bool gm1 = D.scheme == IB_GM1;
+  f.chi_mu_half = gm1 ? T(0) : (T)(0.5 * D.chi * D.mu);
+  f.p_keep = gm1 ? T(0) : T(1);
+  f.psi_w = gm1 ? T(0) : T(1);
   f.rho_dt = (T)(D.rho / D.dt);
   f.dt_mu_rho = (T)(D.dt * D.mu / D.rho);
   f.dt_rho = (T)(D.dt / D.rho);
@@ -825,6 +830,7 @@ int ib_create_grid(const ib_grid_desc *desc, ib_grid_t *out) {
     return fail(IB_ERR_ARG, "H, rho, dt must be > 0 and mu, chi >= 0");
   if (D.precision != IB_FP32 && D.precision != IB_FP64) return fail(IB_ERR_ARG, "precision");
   if (D.kernel != IB_DELTA_PESKIN4 && D.kernel != IB_DELTA_COS4) return fail(IB_ERR_ARG, "kernel");
+  if (D.scheme != IB_GM2 && D.scheme != IB_GM1) return fail(IB_ERR_ARG, "scheme");
   ib_grid_s *g = new ib_grid_s();
   g->desc = D;
   g->dim = D.dim;

@@ -23,13 +23,15 @@ def thin_ellipse(N, sigma=1.0, dt=0.04 / 512, t=0.31, precision="fp64"):
     return run(sc, int(round(t / dt)), precision)
 
 
-def thick_shell(N, mu=0.01, dt=0.08 / 512, t=0.4, precision="fp64"):
+def thick_shell(N, mu=0.01, dt=0.08 / 512, t=0.4, precision="fp64", scheme="gm2", chi=0.6):
     sc = I.thick_shell_2d(n=N, mu=mu, dt=dt, t_end=t)
-    return run(sc, sc.steps, precision)
+    sc.chi = chi
+    return run(sc, sc.steps, precision, scheme)
 
 
-def run(sc, steps, precision):
-    g = ib.Grid(2, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, precision=precision, kernel=sc.kernel, rotate_split=True)
+def run(sc, steps, precision, scheme="gm2"):
+    g = ib.Grid(2, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=precision, kernel=sc.kernel,
+                rotate_split=True, scheme=scheme)
     g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest)
     g.step(steps)
     f = g.fields()

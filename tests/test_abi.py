@@ -4,6 +4,7 @@ import ctypes
 import glob
 import os
 import re
+import subprocess
 
 import paper_1305_3976_gb300 as ib
 
@@ -48,3 +49,43 @@ def test_argument_errors_need_no_gpu():
     h = ctypes.c_void_p()
     assert L.ib_create_grid(ctypes.byref(d), ctypes.byref(h)) == ib.IB_ERR_ARG
     assert b"dim" in L.ib_last_error()
+
+
+def test_bad_scheme_is_rejected_without_gpu():
+    L = ib.lib()
+    d = ib.ib_grid_desc()
+    d.dim, d.H, d.rho, d.mu, d.dt, d.chi = 2, 1.0, 1.0, 0.1, 1e-3, 0.6
+    d.n[0] = d.n[1] = d.n[2] = 16
+    d.scheme = 7
+    h = ctypes.c_void_p()
+    assert L.ib_create_grid(ctypes.byref(d), ctypes.byref(h)) == ib.IB_ERR_ARG
+    assert b"scheme" in L.ib_last_error()
+
+
+def test_struct_layout_matches_the_header(tmp_path):
+    # offsets and sizes of the two structs as a C compiler lays them out
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "ib_gb300.h"\n'
+        "#define F(s, m) printf(#s \" \" #m \" %zu\\n\", offsetof(s, m));\n"
+        "int main(void) {\n"
+        "  F(ib_grid_desc, dim) F(ib_grid_desc, n) F(ib_grid_desc, H) F(ib_grid_desc, rho)\n"
+        "  F(ib_grid_desc, mu) F(ib_grid_desc, dt) F(ib_grid_desc, chi) F(ib_grid_desc, precision)\n"
+        "  F(ib_grid_desc, kernel) F(ib_grid_desc, rotate_split) F(ib_grid_desc, stream)\n"
+        "  F(ib_grid_desc, scheme)\n"
+        "  F(ib_diag, volume) F(ib_diag, div_l2) F(ib_diag, div_max) F(ib_diag, kinetic)\n"
+        "  F(ib_diag, elastic) F(ib_diag, step)\n"
+        '  printf("ib_grid_desc sizeof %zu\\n", sizeof(ib_grid_desc));\n'
+        '  printf("ib_diag sizeof %zu\\n", sizeof(ib_diag));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        s, m, v = line.split()
+        cls = getattr(ib, s)
+        if m == "sizeof":
+            assert ctypes.sizeof(cls) == int(v), line
+        else:
+            assert getattr(cls, m).offset == int(v), line
