@@ -141,11 +141,11 @@ def kernel_bytes(name, cells, nm, ne, w, d=3):
         "force": nm * (d * 8 + 16 + d * w) + 2 * ne * (d * 8 + 4 + 16),
         # locations of X^{n+1/2}, G, one read-modify-write word per stencil node
         "spread": nm * d * (d * (4 + 4 * w) + w + 4 ** d * 2 * w),
-        # u(3), p, psi, f(3), N(u^{n-1})(3) in; R(3), N(u^n)(3) out
-        "rhs": cells * w * (4 * d + 5),
+        # u(3), p, psi, N(u^{n-1})(3) in; R(3), N(u^n)(3) out
+        "rhs": cells * w * (3 * d + 5),
         "mom_sweep_1": cells * w * 2 * d,
         "mom_sweep_2": cells * w * 2 * d,
-        "mom_sweep_3": cells * w * 4 * d,   # e in, u^n in/out, scratch cleared
+        "mom_sweep_3": cells * w * 3 * d,   # e in, u^n in/out
         "psi_sweep_1": cells * w * (d + 5), # u(3), div, p in; psi, div, p out
         "psi_sweep_2": cells * w * 2,
         "psi_sweep_3": cells * w * 4,       # psi, p in; psi, p out

@@ -65,7 +65,7 @@ struct RhsArgs {
   const T *u[3];
   const T *p, *psi;  // p* = p + psi (psi null: p* = p, the first-order variant)
   T *Nold[3];     // in: N(u^{n-1}); out: N(u^n)
-  T *scr[3];      // in: spread force f; out: R = u* - u^n
+  T *scr[3];      // out: R = u* - u^n without the force term (spreading adds dt/rho f)
   T inv_h[3], inv_h2[3];
   T mu, inv_rho, dt;
   int n[3];
@@ -91,7 +91,7 @@ struct MarkerArgs {
   int64_t nm;
   double dt, H;
   double inv_h[3];
-  double inv_vol;       // 1 / h^d
+  double spread_scale;  // dt / (rho h^d): spreading adds dt/rho f to R
   int n[3];
   int dim, kernel, first;
 };

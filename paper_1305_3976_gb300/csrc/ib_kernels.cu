@@ -10,6 +10,8 @@ namespace ibg {
 // Steps 3a-3b in increment form: R_c = u*_c - u^n_c
 //   = dt [ (mu L u_c - G_c p* + f_c) / rho - (3/2 N_c(u^n) - 1/2 N_c(u^{n-1})) ]
 // with p* = p^{n-1/2} + psi^{n-1/2} (0 at n = 0) and N^{1/2} = N(u^0).
+// The kernels below store R without the force term; the spreading kernel,
+// which runs after them, adds dt/rho f_c into R.
 // N is the skew-symmetric form (1/2 u.grad u + 1/2 div(uu)) on the staggered
 // grid: along each axis a the divergence and advective halves with one shared
 // transport velocity A+- (the a-velocity averaged to the two flux points half
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
     }
     // every load first (the stores below may alias nothing the compiler can see)
     T uc[DIM], up[DIM][DIM], um[DIM][DIM], ux[DIM][DIM];  // ux[c][a] = u_a at face + e_a - e_c
-    T f[DIM], nold[DIM], pm[DIM];
+    T nold[DIM], pm[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const T *u = a.u[c];
@@ -54,7 +56,6 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
     const T p0 = a.first ? T(0) : a.p[o] + (a.psi ? a.psi[o] : T(0));
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      f[c] = a.scr[c][o];
       nold[c] = a.first ? T(0) : a.Nold[c][o];
       pm[c] = a.first ? T(0) : a.p[o + dm[c]] + (a.psi ? a.psi[o + dm[c]] : T(0));
     }
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
       }
       const T gp = (p0 - pm[c]) * a.inv_h[c];
       const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[c];
-      R[c] = a.dt * ((a.mu * lap - gp + f[c]) * a.inv_rho - Nh);
+      R[c] = a.dt * ((a.mu * lap - gp) * a.inv_rho - Nh);
       Nn[c] = adv;
     }
 #pragma unroll
@@ -142,8 +143,7 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
     else if (C == 1) get4(uA, R(ym, z), x0, nx, 0, Um[A]);
     else get4(uA, R(y, zm), x0, nx, 0, Um[A]);
   }
-  T f[4], nold[4], P0[4], Pm[4];
-  ld4(a.scr[C] + ro + x0, f);
+  T nold[4], P0[4], Pm[4];
   if (!a.first) {
     T t0[4], t1[4];
     ld4(a.Nold[C] + ro + x0, nold);
@@ -183,7 +183,7 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
     }
     const T gp = (P0[e] - Pm[e]) * a.inv_h[C];
     const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[e];
-    Rv[e] = a.dt * ((a.mu * lap - gp + f[e]) * a.inv_rho - Nh);
+    Rv[e] = a.dt * ((a.mu * lap - gp) * a.inv_rho - Nh);
     Nn[e] = adv;
   }
   st4(a.scr[C] + ro + x0, Rv);

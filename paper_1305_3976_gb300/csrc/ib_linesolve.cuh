@@ -366,8 +366,6 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
 #pragma unroll
         for (int e = 0; e < 4; ++e) uu[e] += v[r][e];
         st4(a.uo[comp] + base + i0, uu);
-        const T zero[4] = {T(0), T(0), T(0), T(0)};
-        st4(F + base + i0, zero);
       }
     } else if (EPI == EPI_P && vec) {
       if (i0 < nx) {
@@ -393,7 +391,6 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
             F[o] = v[r][e];
           } else if (EPI == EPI_ADDU) {
             a.uo[comp][o] = old[e] + v[r][e];
-            F[o] = T(0);
           } else {
             F[o] = v[r][e];
             a.p[o] = old[e] + v[r][e];
@@ -581,16 +578,14 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) stv<VW>(F + o0 + e * stride, v[e]);
   } else {
-    // scratch / psi stores first, then every load of the old values, then the
-    // sums: no load waits behind a store
+    // psi stores first, then every load of the old values, then the sums:
+    // no load waits behind a store
     T *tgt = EPI == EPI_ADDU ? a.uo[comp] : a.p;
-    const T zero[VW] = {};
+    if (EPI == EPI_P) {
 #pragma unroll
-    for (int e = 0; e < CH; ++e)
-      if (FULL || e < len) {
-        if (EPI == EPI_ADDU) stv<VW>(F + o0 + e * stride, zero);  // clear the scratch
-        else stv<VW>(F + o0 + e * stride, v[e]);                   // psi
-      }
+      for (int e = 0; e < CH; ++e)
+        if (FULL || e < len) stv<VW>(F + o0 + e * stride, v[e]);
+    }
 #pragma unroll
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) {

@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
   }
 }
 
-// Step 2b: f_c(node) += G_c prod_a phi_a / h^d at X^{n+1/2} with global
-// atomics, one lane group per (marker, c), 128-bit vector atomics per row
+// Step 2b: f_c(node) += G_c prod_a phi_a / h^d at X^{n+1/2}, added as
+// dt/rho f_c into the momentum increment R that the right-hand-side kernel
+// stored (Step 3b), with global atomics, one lane group per (marker, c),
+// 128-bit vector atomics per row
 // where the row segment allows.  Markers are numbered in Morton order of
 // their initial positions, so neighbouring groups update neighbouring nodes.
 template <typename T, int DIM>
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0,
   StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w);
   if (!L.valid) return;
   T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
-  const T val = ((const T *)m.G[L.c])[L.k] * (T)m.inv_vol * L.wrow;
+  const T val = ((const T *)m.G[L.c])[L.k] * (T)m.spread_scale * L.wrow;
   T v[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = val * L.wx[i];

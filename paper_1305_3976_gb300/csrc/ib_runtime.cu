@@ -2,16 +2,17 @@
 //
 // One ib_grid_t owns, on the current device:
 //   fields  (precision T): u[d], p, psi, Nold[d] = N(u^{n-1}), div = D.u^n,
-//           scr[d] (spread force f -> momentum increment R -> sweep results;
-//           zero between steps), all in one allocation;
+//           scr[d] (momentum increment R, to which spreading adds dt/rho f,
+//           then the sweep results), all in one allocation;
 //   markers (FP64 SoA): X, Xh = X^{n+1/2}, U = U^n, Uold = U^{n-1}, G, plus
 //           the force connections as CSR by marker and as an edge list;
 //   line-solve tables: lam^k (k = 0..n_a) per axis for the momentum operator
 //           (r = mu dt / (2 rho h_a^2)) and the psi operator (r = 1 / h_a^2).
-// A step is 10 launches in 3D (8 in 2D): interp, force, spread, rhs, d
-// momentum sweeps, d psi sweeps.  Steps after the first replay a CUDA graph
-// (one per split-order phase) on a library-owned stream that is ordered
-// against the caller's stream with events.
+// A step is 11 launches in 3D (9 in 2D): interp, update, force, rhs, spread,
+// d momentum sweeps, d psi sweeps.
+// Steps after the first replay a CUDA graph (one per split-order phase) on a
+// library-owned stream that is ordered against the caller's stream with
+// events.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -202,8 +203,8 @@ MarkerArgs marker_args(ib_grid_s *g, bool first) {
   m.nm = g->nm;
   m.dt = g->desc.dt;
   m.H = g->desc.H;
-  m.inv_vol = 1.0;
-  for (int a = 0; a < d; ++a) m.inv_vol /= g->h[a];
+  m.spread_scale = g->desc.dt / g->desc.rho;
+  for (int a = 0; a < d; ++a) m.spread_scale /= g->h[a];
   m.dim = d;
   m.kernel = g->desc.kernel;
   m.first = first ? 1 : 0;
@@ -223,6 +224,8 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   MarkerArgs m = marker_args(g, first);
   const T *uc[3] = {(const T *)g->u[0], (const T *)g->u[1], (const T *)g->u[2]};
   T *sc[3] = {(T *)g->scr[0], (T *)g->scr[1], (T *)g->scr[2]};
+  // Steps 1a-2a; spreading (Step 2b) follows the right-hand side, into which
+  // it adds dt/rho f
   if ((rc = mark(0))) return rc;
   IB_CUDA(launch_interp<T>(m, uc, g->s));
   if ((rc = mark(1))) return rc;
@@ -230,8 +233,6 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   if ((rc = mark(2))) return rc;
   IB_CUDA(launch_force<T>(m, g->s));
   if ((rc = mark(3))) return rc;
-  IB_CUDA(launch_spread<T>(m, sc, g->s));
-  if ((rc = mark(4))) return rc;
   // Steps 3a-3b
   RhsArgs<T> ra;
   memset(&ra, 0, sizeof(ra));
@@ -251,6 +252,9 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   ra.dt = (T)g->desc.dt;
   ra.first = first ? 1 : 0;
   IB_CUDA(launch_rhs<T>(d, ra, g->s));
+  if ((rc = mark(4))) return rc;
+  // Step 2b: R += dt/rho S(X^{n+1/2}) G
+  IB_CUDA(launch_spread<T>(m, sc, g->s));
   if ((rc = mark(5))) return rc;
   // Steps 3c-3d (+ z): increment-form Douglas sweeps on the scratch fields
   SweepArgs<T> sa;
@@ -475,7 +479,7 @@ int ensure_loc(ib_grid_s *g) {
 }
 
 // Autotuner: for every axis, time each candidate sweep configuration on the
-// d scratch fields (zero outside a step) with the plain load/store sweep,
+// d scratch fields (zero before the first step) with the plain load/store sweep,
 // 1 + 3 launches each, and keep the fastest; the step's sweeps along that
 // axis then use it.
 template <typename T>
@@ -986,20 +990,20 @@ int ib_profile_step(ib_grid_t g, int n_steps, float *kernel_ms, int max_kernels,
       break;
     }
     // marks: 0 before interp, 1 after interp, 2 after update, 3 after force,
-    // 4 after spread, 5 after rhs, 6 + s after the s-th momentum sweep, 9 + s
+    // 4 after rhs, 5 after spread, 6 + s after the s-th momentum sweep, 9 + s
     // after the s-th psi sweep (s in split order)
     float ms;
+    const int span[5][2] = {{0, 1}, {1, 2}, {2, 3}, {4, 5}, {3, 4}};  // interp, update, force, spread, rhs
     for (int k = 0; k < 5; ++k) {
-      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      cudaEventElapsedTime(&ms, ev[span[k][0]], ev[span[k][1]]);
       tot[k] += ms;
     }
-    const int last_m = 6 + g->dim - 1;
     for (int q = 0; q < g->dim; ++q) {
       cudaEventElapsedTime(&ms, ev[5 + q], ev[6 + q]);
       tot[5 + q] += ms;
     }
     for (int q = 0; q < g->dim; ++q) {
-      cudaEventElapsedTime(&ms, q == 0 ? ev[last_m] : ev[8 + q], ev[9 + q]);
+      cudaEventElapsedTime(&ms, q == 0 ? ev[6 + g->dim - 1] : ev[8 + q], ev[9 + q]);
       tot[8 + q] += ms;
     }
     g->step++;

@@ -36,6 +36,7 @@ def test_error_strings_without_gpu():
     assert L.ib_error_string(ib.IB_ERR_ARG) == b"invalid argument"
     assert L.ib_error_string(0) == b"ok"
     assert L.ib_kernel_name(0) == b"interp"
+    assert L.ib_kernel_name(4) == b"rhs" and L.ib_kernel_name(11) == b""
 
 
 def test_argument_errors_need_no_gpu():
