@@ -84,16 +84,20 @@ struct MarkerArgs {
   void *locI_w;     // [2d][nm][4] field precision
   int32_t *locS_b;  // [2d][nm] of X^{n+1/2} (spreading)
   void *locS_w;
+  void *locS_f;     // [d][nm] field precision: fraction of X^{n+1/2} / h on the own-axis offset
   const int64_t *row;   // CSR over markers: neighbours of marker a are
   const int32_t *col;   //   col[row[a] .. row[a+1]) with
   const double *kap;    //   spring constants kap[] and rest lengths rest[]
   const double *rest;
+  const void *kapT, *restT;  // the same in the field precision
   int64_t nm;
   double dt, H;
   double inv_h[3];
   double spread_scale;  // dt / (rho h^d): spreading adds dt/rho f to R
+  float h32[3], inv_n32[3];  // h_a and 1 / n_a for the location-based force
   int n[3];
   int dim, kernel, first;
+  int frac_force;       // force from the stored locations of X^{n+1/2} (FP32 fields)
 };
 
 // adjoint step (see ib_adjoint.cu)

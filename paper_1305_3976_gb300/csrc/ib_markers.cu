@@ -67,15 +67,17 @@ __device__ __forceinline__ void weights(T f, int kernel, T (&w)[4]) {
 // Location of coordinate X on axis a for both MAC offsets: first stencil
 // node b[2a + o] and the 4 weights w[2a + o][0..3] (stored as 4 consecutive
 // values of the field precision).
+// With lf, the own-axis fraction f0 is stored as well.
 template <typename T>
 __device__ __forceinline__ void store_location(const MarkerArgs &m, double X, int a, long long k, int32_t *lb,
-                                               T *lw) {
+                                               T *lw, T *lf = nullptr) {
   int b0, b1;
   T f0, f1, w[4];
   locate2<T>(X, m.inv_h[a], b0, f0, b1, f1);
   const long long s0 = (2 * a) * m.nm + k, s1 = (2 * a + 1) * m.nm + k;
   lb[s0] = b0;
   lb[s1] = b1;
+  if (lf) lf[a * m.nm + k] = f0;
   weights<T>(f0, m.kernel, w);
   st4(lw + 4 * s0, w);
   weights<T>(f1, m.kernel, w);
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
   m.X[c][k] = Xn;
   ((T *)m.Uold[c])[k] = Ut;
   (void)nm;
-  store_location<T>(m, Xh, c, k, m.locS_b, (T *)m.locS_w);
+  store_location<T>(m, Xh, c, k, m.locS_b, (T *)m.locS_w, (T *)m.locS_f);
   store_location<T>(m, Xn, c, k, m.locI_b, (T *)m.locI_w);
 }
 
@@ -162,15 +164,16 @@ struct StencilLanes {
   }
 };
 
-// 4 consecutive values r[xs .. xs+3] of a row, periodic in x; two aligned
-// 128-bit loads when the 8-float block around xs lies inside the row
+// 4 consecutive values r[xs .. xs+3] of a row, periodic in x; aligned
+// 128-bit loads (the second only when xs is not 4-aligned) when the 8-float
+// block around xs lies inside the row
 __device__ __forceinline__ void row4(const float *r, int xs, int nx, float (&v)[4]) {
   const int a0 = xs & ~3;
   if ((nx & 3) == 0 && a0 + 8 <= nx) {
-    const float4 p = __ldg(reinterpret_cast<const float4 *>(r + a0));
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(r + a0 + 4));
-    const float t[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
     const int off = xs - a0;
+    const float4 p = __ldg(reinterpret_cast<const float4 *>(r + a0));
+    const float4 q = off ? __ldg(reinterpret_cast<const float4 *>(r + a0 + 4)) : p;
+    const float t[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = off == 0 ? t[i] : off == 1 ? t[i + 1] : off == 2 ? t[i + 2] : t[i + 3];
   } else {
@@ -226,10 +229,16 @@ __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *con
 
 // Step 2a over the force connections at X^{n+1/2}: 8 lanes per marker share
 // its CSR row (lane j takes connections j, j+8, ...) and add their partial
-// forces with shuffles.  Differences X_b - X_a are taken in FP64 and reduced
-// to the nearest periodic image; the spring arithmetic runs in the field
-// precision.
-template <typename T, int DIM>
+// forces with shuffles; the spring arithmetic runs in the field precision.
+// The difference X_b - X_a, reduced to the nearest periodic image, comes
+//   FRAC = false: from the FP64 positions;
+//   FRAC = true (FP32 fields): from the stored locations of X^{n+1/2},
+//     X_q = h_q (i_q + 1 + f_q) with the integer first stencil node i_q and
+//     the fraction f_q in [0, 1): X_b - X_a = h_q (di + df) with the integer
+//     di = i_b - i_a, shifted by whole periods n_q in integer arithmetic, and
+//     the FP32 fraction difference df.  No FP64 instruction, and the same
+//     accuracy as rounding the FP64 difference to FP32.
+template <typename T, int DIM, bool FRAC>
 __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
   const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned a = gt >> 3;
@@ -239,9 +248,19 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
 #pragma unroll
   for (int q = 0; q < DIM; ++q) g[q] = T(0);
   if (valid) {
+    const unsigned nm = (unsigned)m.nm;
     double xa[DIM];
+    int ia[DIM];
+    T fa[DIM];
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) xa[q] = m.Xh[q][a];
+    for (int q = 0; q < DIM; ++q) {
+      if (FRAC) {
+        ia[q] = m.locS_b[(2 * q) * nm + a];
+        fa[q] = ((const T *)m.locS_f)[q * nm + a];
+      } else {
+        xa[q] = m.Xh[q][a];
+      }
+    }
     const T H = (T)m.H, invH = (T)(1.0 / m.H);
     const long long e1 = m.row[a + 1];
     for (long long e = m.row[a] + lane8; e < e1; e += 8) {
@@ -249,13 +268,26 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
       T d[DIM], len2 = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
-        d[q] = (T)(m.Xh[q][b] - xa[q]);
-        d[q] -= H * rint(d[q] * invH);  // nearest periodic image
+        if (FRAC) {
+          const int di = m.locS_b[(2 * q) * nm + b] - ia[q];
+          const T df = ((const T *)m.locS_f)[q * nm + b] - fa[q];
+          const int sh = __float2int_rn(((float)di + (float)df) * m.inv_n32[q]);
+          d[q] = ((T)(di - sh * m.n[q]) + df) * (T)m.h32[q];
+        } else {
+          d[q] = (T)(m.Xh[q][b] - xa[q]);
+          d[q] -= H * rint(d[q] * invH);  // nearest periodic image
+        }
         len2 += d[q] * d[q];
       }
-      T scale = (T)m.kap[e];
-      const double L = m.rest[e];
-      if (L != 0.0) scale *= T(1) - (T)L / sqrt(len2);
+      T scale, L;
+      if (FRAC) {
+        scale = ((const T *)m.kapT)[e];
+        L = ((const T *)m.restT)[e];
+      } else {
+        scale = (T)m.kap[e];
+        L = (T)m.rest[e];
+      }
+      if (L != T(0)) scale *= T(1) - L / sqrt(len2);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) g[q] += scale * d[q];
     }
@@ -339,8 +371,13 @@ template <typename T>
 cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
   const unsigned g = nblocks(m.nm * 8, 256);
-  if (m.dim == 2) k_force<T, 2><<<g, 256, 0, s>>>(m);
-  else k_force<T, 3><<<g, 256, 0, s>>>(m);
+  if (m.frac_force) {
+    if (m.dim == 2) k_force<T, 2, true><<<g, 256, 0, s>>>(m);
+    else k_force<T, 3, true><<<g, 256, 0, s>>>(m);
+  } else {
+    if (m.dim == 2) k_force<T, 2, false><<<g, 256, 0, s>>>(m);
+    else k_force<T, 3, false><<<g, 256, 0, s>>>(m);
+  }
   return cudaGetLastError();
 }
 

@@ -157,6 +157,8 @@ struct ib_grid_s {
   void *U[3] = {}, *Uold[3] = {}, *G[3] = {};  // field precision
   int32_t *locI_b = nullptr, *locS_b = nullptr;  // [2d][nm] grid locations (see MarkerArgs)
   void *locI_w = nullptr, *locS_w = nullptr;      // [2d][nm][4] their weights
+  void *locS_f = nullptr;       // [d][nm] own-axis fraction of X^{n+1/2}
+  void *kapT = nullptr, *restT = nullptr;  // [2ne] CSR spring data in the field precision
   int64_t *row = nullptr;
   int32_t *col = nullptr, *edges = nullptr, *tris = nullptr;
   double *kap = nullptr, *rest = nullptr, *ekap = nullptr, *erest = nullptr;
@@ -196,6 +198,14 @@ MarkerArgs marker_args(ib_grid_s *g, bool first) {
   m.locI_w = g->locI_w;
   m.locS_b = g->locS_b;
   m.locS_w = g->locS_w;
+  m.locS_f = g->locS_f;
+  m.kapT = g->kapT;
+  m.restT = g->restT;
+  for (int a = 0; a < 3; ++a) {
+    m.h32[a] = (float)g->h[a];
+    m.inv_n32[a] = 1.0f / (float)g->n[a];
+  }
+  m.frac_force = g->prec == IB_FP32 ? 1 : 0;
   m.row = g->row;
   m.col = g->col;
   m.kap = g->kap;
@@ -355,6 +365,7 @@ int upload_markers(ib_grid_s *g) {
   for (int64_t a = 0; a < nm; ++a) row[a + 1] += row[a];
   std::vector<int32_t> col(2 * ne), cedge(2 * ne);
   std::vector<double> kap(2 * ne), rest(2 * ne);
+  std::vector<float> kapf(g->esz == 4 ? 2 * ne : 0), restf(g->esz == 4 ? 2 * ne : 0);
   std::vector<int64_t> fill(row.begin(), row.end() - 1);
   for (int64_t e = 0; e < ne; ++e) {
     const int32_t a = E[2 * e], b = E[2 * e + 1];
@@ -395,6 +406,9 @@ int upload_markers(ib_grid_s *g) {
   const size_t o_lsb = take(sizeof(int32_t) * 2 * d * (nm + 1));
   const size_t o_lif = take(es * 4 * 2 * d * (nm + 1));
   const size_t o_lsf = take(es * 4 * 2 * d * (nm + 1));
+  const size_t o_lff = take(es * d * (nm + 1));
+  const size_t o_kt = take(es * (2 * ne + 1));
+  const size_t o_rt = take(es * (2 * ne + 1));
   if (cudaMalloc(&g->mk, off) != cudaSuccess) return fail(IB_ERR_OOM, "marker allocation of %zu bytes failed", off);
   char *base = (char *)g->mk;
   double *md = (double *)(base + o_m);
@@ -411,6 +425,9 @@ int upload_markers(ib_grid_s *g) {
   g->locS_b = (int32_t *)(base + o_lsb);
   g->locI_w = base + o_lif;
   g->locS_w = base + o_lsf;
+  g->locS_f = base + o_lff;
+  g->kapT = base + o_kt;
+  g->restT = base + o_rt;
   g->row = (int64_t *)(base + o_row);
   g->col = (int32_t *)(base + o_col);
   g->kap = (double *)(base + o_kap);
@@ -431,6 +448,17 @@ int upload_markers(ib_grid_s *g) {
     IB_CUDA(cudaMemcpyAsync(g->cedge, cedge.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    if (es == 4) {
+      for (int64_t e = 0; e < 2 * ne; ++e) {
+        kapf[e] = (float)kap[e];
+        restf[e] = (float)rest[e];
+      }
+      IB_CUDA(cudaMemcpyAsync(g->kapT, kapf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+      IB_CUDA(cudaMemcpyAsync(g->restT, restf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    } else {
+      IB_CUDA(cudaMemcpyAsync(g->kapT, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+      IB_CUDA(cudaMemcpyAsync(g->restT, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    }
     IB_CUDA(cudaMemcpyAsync(g->edges, E.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->ekap, g->hK.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->erest, g->hR.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
@@ -786,7 +814,9 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
         }
         am.first = first;
         IB_CUDA(adjoint_markers_pre<T>(am, u, g->s));
-        IB_CUDA(launch_force<T>(marker_args(g, first), g->s));
+        MarkerArgs mf = marker_args(g, first);
+        mf.frac_force = 0;  // the stored fractions belong to the forward run, not to X^{n+1/2} here
+        IB_CUDA(launch_force<T>(mf, g->s));
         IB_CUDA(cudaMemsetAsync(Xhb, 0, sizeof(double) * d * nm, g->s));
         const T *rbc[3] = {f.rb[0], f.rb[1], f.rb[2]};
         IB_CUDA(adjoint_markers_post<T>(am, rbc, f.dt_rho, u, f.ub, g->s));

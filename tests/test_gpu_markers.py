@@ -1,0 +1,108 @@
+"""Interpolation and spreading paths against the oracle (FP64 fields).
+
+The marker kernels work on patches of consecutive markers whose stencils fit
+a shared-memory box, and take a direct path when they do not.  These cases
+exercise both paths and the periodic wrap of unwrapped positions:
+  - markers scattered uniformly through the box, joined by long connections
+    (most patches exceed the box budget: direct path);
+  - a membrane translated by one period in x (unwrapped node indices in
+    [n, 2n): wrapped on loads and stores, the results match the untranslated
+    oracle run to rounding);
+  - a 2D fiber straddling the periodic boundary in both directions.
+Tolerances as in tests/test_gpu_step.py.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1305_3976_gb300 as ib
+from paper_1305_3976_gb300 import inputs as I
+
+from test_gpu_step import compare, psi_bound, small_ellipsoid
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(sc, steps, precision="fp64"):
+    P = O.params(sc.dim, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
+    ora = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
+    g = ib.Grid(sc.dim, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=precision,
+                kernel=sc.kernel, rotate_split=True)
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+    ora.step(steps)
+    g.step(steps)
+    e = compare(ora, g)
+    g.close()
+    return e
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_scattered_markers_direct_path(dim):
+    n = 32 if dim == 3 else 64
+    X = I.random_markers(dim, 700, seed=11)
+    edges = np.stack([np.arange(699), np.arange(1, 700)], axis=1).astype(np.int32)
+    sc = I.Scene(dim=dim, n=(n,) * dim, rho=1.0, mu=0.05, dt=2e-4, steps=3, X=X, edges=edges,
+                 kappa=np.full(699, 0.5), rest=np.zeros(699))
+    e = run_pair(sc, 3)
+    assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
+    assert e["X"] < 1e-13, e
+
+
+def test_membrane_one_period_away():
+    sc = small_ellipsoid(n=32, nu=8)
+    sc.X = sc.X + np.array([1.0, 0.0, -1.0])
+    e = run_pair(sc, 3)
+    assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
+    assert e["X"] < 1e-13, e
+
+
+def test_fiber_across_the_periodic_boundary_2d():
+    sc = I.thin_ellipse_2d(n=64, ns=256)
+    sc.X = sc.X + np.array([0.5, 0.5])          # centred on the corner (1, 1) of the box
+    e = run_pair(sc, 5)
+    assert e["u"] < psi_bound(sc, 5) and e["p"] < psi_bound(sc, 5), e
+    assert e["X"] < 1e-13, e
+
+
+def test_fp32_patches_match_fp64_patches_at_full_size():
+    sc = I.ellipsoid_3d(n=128, nu=64)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=prec, rotate_split=True)
+        g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+        g.step(3)
+        out[prec] = (g.velocity().astype(np.float64), g.markers())
+        g.close()
+    u32, X32 = out["fp32"]
+    u64, X64 = out["fp64"]
+    assert np.linalg.norm(u32 - u64) <= 1e-5 * np.linalg.norm(u64)
+    assert np.max(np.abs(X32 - X64)) <= 1e-6 / 128
+
+
+def test_fp32_force_from_locations_with_rest_length_and_closure():
+    # FP32 fields compute connection differences from the stored grid
+    # locations: the cylinder's axial connections (rest length L h_r) close
+    # through the periodic box, so their differences need the image shift
+    sc = I.cylinder_3d(n=24, dt=2e-3)
+    e = run_pair(sc, 2, "fp32")
+    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+    assert e["X"] < 1e-6 / 24, e
+
+
+def test_fp32_force_from_locations_across_the_boundary():
+    # tiled ellipses carried through the top of the periodic box (FP32 fields)
+    sc = I.tiled_ellipses_2d(tiles=2, n_per_tile=32, dt=4e-3)
+    P = O.params(2, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
+    ora = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest, u0=sc.extra["u0"])
+    g = ib.Grid(2, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision="fp32", kernel=sc.kernel,
+                rotate_split=True)
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest)
+    g.set_velocity(sc.extra["u0"])
+    ora.step(110)
+    g.step(110)
+    assert g.markers()[:, 1].max() > sc.H
+    e = compare(ora, g)
+    g.close()
+    h = sc.H / sc.n[0]
+    assert e["u"] < 1e-4, e
+    assert e["X"] < 1e-4 * h, e
