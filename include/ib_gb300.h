@@ -39,7 +39,7 @@ enum {
   IB_ERR_OOM = -2,       /* device or host allocation failed                    */
   IB_ERR_CUDA = -3,      /* a CUDA runtime call failed (see ib_last_error)      */
   IB_ERR_NONFINITE = -4, /* a NaN or Inf was found in the state                 */
-  IB_ERR_TIMEOUT = -5,   /* reserved: a bounded device-side wait ran out        */
+  IB_ERR_TIMEOUT = -5,   /* a bounded device-side wait ran out (ib_diagnostics) */
   IB_ERR_STATE = -6      /* call not allowed in the grid's current state        */
 };
 
@@ -146,7 +146,10 @@ int ib_read_markers(ib_grid_t g, double *X, int64_t n, int dst_on_device);
 int ib_set_markers(ib_grid_t g, const double *X, int64_t n, int src_on_device);
 
 /* FP64 diagnostics of the current state; synchronises the grid's stream.
- * Returns IB_ERR_NONFINITE (after filling *out) if any value is NaN or Inf. */
+ * Returns IB_ERR_NONFINITE (after filling *out) if any value is NaN or Inf,
+ * and IB_ERR_TIMEOUT if, since the last such report, a kernel of this
+ * process gave up a bounded wait for its staged copies (results of that
+ * launch are then not to be trusted). */
 int ib_diagnostics(ib_grid_t g, ib_diag *out);
 
 /* Release every device and host resource of the grid. */

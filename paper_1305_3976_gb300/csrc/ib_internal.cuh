@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a IB-GM implementation (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,6 +101,20 @@ struct MarkerArgs {
   int frac_force;       // force from the stored locations of X^{n+1/2} (FP32 fields)
 };
 
+// strided line solves staged by TMA (see ib_sweep_tma.cu): FP32, y and z
+// lines, plain load/store sweeps; autotuner candidate id kTmaCfg
+constexpr int kTmaCfg = 11;
+struct SweepTmaMaps {
+  CUtensorMap in[3], out[3];  // per field: boxes of 32 x columns x (part of) a line
+  int nfields;
+};
+bool sweep_tma_ok(const SweepArgs<float> &a, int axis);
+void sweep_tma_shape(int nl, int *ch, int *w);
+cudaError_t launch_sweep_tma(int axis, int nfields, const SweepArgs<float> &a, cudaStream_t s);
+// process-wide flag set by a kernel whose bounded wait ran out; returns its
+// value and clears it
+int take_wait_timeout();
+
 // adjoint step (see ib_adjoint.cu)
 template <typename T>
 struct AdjFields {
@@ -156,7 +171,7 @@ template <typename T>
 cudaError_t launch_sweep(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s,
                          int cfg = -1);
 int sweep_candidates(int axis, int nl, int nx, bool dbl, int *out, int max);
-void sweep_config_shape(int axis, int cfg, int *a, int *b, int *c);
+void sweep_config_shape(int axis, int cfg, int nl, int *a, int *b, int *c);
 template <typename T>
 cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s);
 template <typename T>

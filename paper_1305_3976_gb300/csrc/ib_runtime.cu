@@ -172,6 +172,7 @@ struct ib_grid_s {
   bool loc_valid = false;       // locI holds the grid locations of the current X
   bool tuned = false;
   int tune[3] = {-1, -1, -1};   // sweep configuration per axis (autotuned)
+  int tune_r[3] = {-1, -1, -1}; // the best one for the sweeps with a prologue or epilogue (no TMA kernel)
   bool fixed[3] = {false, false, false};  // set by ib_fix_sweep_config: not timed
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
@@ -285,7 +286,8 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   for (int st = 0; st < d; ++st) {
     const int ax = order[st];
     sa.co = coef_of<T>(g->coef[0][ax]);
-    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, st == d - 1 ? EPI_ADDU : EPI_STORE, d, sa, g->s, g->tune[ax]));
+    const bool last = st == d - 1;
+    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, last ? EPI_ADDU : EPI_STORE, d, sa, g->s, last ? g->tune_r[ax] : g->tune[ax]));
     if ((rc = mark(6 + st))) return rc;
   }
   // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
@@ -296,7 +298,8 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     sa.co = coef_of<T>(g->coef[1][ax]);
     const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
     const int epi = st == d - 1 ? EPI_P : EPI_STORE;
-    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s, g->tune[ax]));
+    const bool plain = pro == PRO_LOAD && epi == EPI_STORE;
+    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s, plain ? g->tune[ax] : g->tune_r[ax]));
     if ((rc = mark(9 + st))) return rc;
   }
   return IB_OK;
@@ -530,7 +533,7 @@ int autotune_t(ib_grid_s *g) {
     sa.co = coef_of<T>(g->coef[0][ax]);
     int cand[16];
     const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 16);
-    float best = 1e30f;
+    float best = 1e30f, best_r = 1e30f;
     for (int i = 0; i < nc && !rc; ++i) {
       if (launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, cand[i]) != cudaSuccess) {
         rc = fail(IB_ERR_CUDA, "autotune launch");
@@ -548,6 +551,10 @@ int autotune_t(ib_grid_s *g) {
       if (ms < best) {
         best = ms;
         g->tune[ax] = cand[i];
+      }
+      if (cand[i] != kTmaCfg && ms < best_r) {
+        best_r = ms;
+        g->tune_r[ax] = cand[i];
       }
     }
   }
@@ -1052,7 +1059,7 @@ int ib_sweep_config(ib_grid_t g, int axis, int *cfg) {
   if (!rc) rc = leave(g);
   if (rc) return rc;
   const int id = g->tune[axis];
-  sweep_config_shape(axis, id, &cfg[1], &cfg[2], &cfg[3]);
+  sweep_config_shape(axis, id, g->n[axis], &cfg[1], &cfg[2], &cfg[3]);
   cfg[0] = id;
   return IB_OK;
 }
@@ -1066,6 +1073,7 @@ int ib_fix_sweep_config(ib_grid_t g, int axis, int id) {
   for (int i = 0; i < nc; ++i) ok = ok || cand[i] == id;
   if (!ok) return fail(IB_ERR_ARG, "configuration %d is not a candidate for axis %d of this grid", id, axis);
   g->tune[axis] = id;
+  g->tune_r[axis] = id == kTmaCfg ? -1 : id;
   g->fixed[axis] = true;
   return IB_OK;
 }
@@ -1164,6 +1172,7 @@ int ib_diagnostics(ib_grid_t g, ib_diag *out) {
   out->elastic = acc[4];
   out->step = g->step;
   if ((rc = leave(g))) return rc;
+  if (take_wait_timeout()) return fail(IB_ERR_TIMEOUT, "a bounded device wait ran out in an earlier launch");
   if (acc[5] != 0.0 || !isfinite(acc[0]) || !isfinite(acc[2]) || !isfinite(acc[3]))
     return fail(IB_ERR_NONFINITE, "%g non-finite values in the state", acc[5]);
   return IB_OK;

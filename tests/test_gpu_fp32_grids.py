@@ -1,0 +1,79 @@
+"""FP32 fields on unusual 3D grids against the FP64 oracle:
+
+  - sizes that are not multiples of the kernels' tiles in y and z, with a
+    random velocity field so every periodic neighbour carries data;
+  - long x rows (n_x = 256 with a membrane, n_x = 512);
+  - the first-order variant (p* = p, psi unused).
+FP32 tolerances: 1e-4 relative velocity and pressure (as for the other FP32
+comparisons with the FP64 oracle), markers 1e-6 h.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1305_3976_gb300 as ib
+from paper_1305_3976_gb300 import inputs as I
+
+from test_gpu_step import compare, make_pair, small_ellipsoid
+
+pytestmark = pytest.mark.gpu
+
+
+def fluid_scene(n, seed=7):
+    return I.Scene(dim=3, n=n, rho=1.3, mu=0.02, dt=1e-3, steps=0, X=np.zeros((0, 3)),
+                   edges=np.zeros((0, 2), np.int32), kappa=np.zeros(0), rest=np.zeros(0))
+
+
+@pytest.mark.parametrize("n", [(24, 30, 42), (8, 9, 11), (36, 40, 17)])
+def test_ragged_sizes_fluid_only(n):
+    sc = fluid_scene(n)
+    u0 = I.random_velocity(3, n, seed=7, amplitude=0.3)
+    ora, g = make_pair(sc, "fp32", u0=u0)
+    for k in (1, 3):
+        ora.step(k)
+        g.step(k)
+        e = compare(ora, g)
+        assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+    assert g.diagnostics()["step"] == 4
+    g.close()
+
+
+def test_wide_rows_with_membrane():
+    X, E, K, R, T = I.ellipsoid_membrane(16, (0.2, 0.25, 0.3), (0.5, 0.5, 0.5))
+    sc = I.Scene(dim=3, n=(256, 24, 20), rho=1.0, mu=0.05, dt=2e-4, steps=0, X=X, edges=E, kappa=K, rest=R,
+                 tris=T)
+    u0 = I.random_velocity(3, sc.n, seed=3, amplitude=0.1)
+    ora, g = make_pair(sc, "fp32", u0=u0)
+    ora.step(2)
+    g.step(2)
+    e = compare(ora, g)
+    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+    assert e["X"] < 1e-6 / 24, e
+    g.close()
+
+
+def test_first_order_variant_fp32():
+    sc = small_ellipsoid(n=32, nu=8)
+    P = O.params(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True, scheme="gm1")
+    ora = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
+    g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision="fp32", kernel=sc.kernel,
+                rotate_split=True, scheme="gm1")
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+    ora.step(4)
+    g.step(4)
+    e = compare(ora, g)
+    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+    g.close()
+
+
+def test_rows_of_512():
+    # the psi operator along x has condition number up to 1 + 4 * 512^2, so
+    # FP32 pressure carries more rounding here (measured 2e-4)
+    sc = fluid_scene((512, 8, 8))
+    u0 = I.random_velocity(3, sc.n, seed=5, amplitude=0.3)
+    ora, g = make_pair(sc, "fp32", u0=u0)
+    ora.step(2)
+    g.step(2)
+    e = compare(ora, g)
+    assert e["u"] < 1e-4 and e["p"] < 1e-3, e
+    g.close()
