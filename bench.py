@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--nu", type=int, default=64)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, line-solve, e2e and CPU legs")
+    ap.add_argument("--line-solve-only", action="store_true",
+                    help="run only the line-solve microbench (one JSON line with its table), e.g. under a profiler")
     ap.add_argument("--sweep-config", default=None,
                     help="comma-separated line-solve configuration ids per axis (as printed under "
                          "sweep_configs) to use instead of autotuning, e.g. to profile a run's choice")
@@ -185,6 +187,49 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def line_solve_leg(ib, torch, dev, flush, hbm, sizes=(128, 256, 512), precisions=("f32", "f64")):
+    """Sec. 6.1's Poisson-comparison problem: (1 - D_xx)(1 - D_yy)(1 - D_zz) psi
+    = f with f = sin 2 pi x cos 2 pi y cos 2 pi z at the cell centres of the
+    unit cube, three line-solve sweeps through ib_split_solve.  r = 1/h^2 (the
+    psi operator) everywhere, plus the momentum operator's r = mu dt / (2 rho
+    h^2) of the benchmark workload at 512^3 FP32.  L2 is flushed before every
+    timed solve; bytes = 3 sweeps x (read + write) of the field."""
+    rows = []
+    for N in sizes:
+        for prec in precisions:
+            dtype = torch.float32 if prec == "f32" else torch.float64
+            c = (torch.arange(N, device=dev, dtype=torch.float64) + 0.5) / N
+            z, y, x = torch.meshgrid(c, c, c, indexing="ij")
+            f = (torch.sin(2 * torch.pi * x) * torch.cos(2 * torch.pi * y) * torch.cos(2 * torch.pi * z)).to(dtype)
+            del x, y, z
+            psi = torch.empty_like(f)
+            kinds = [("psi", float(N * N))]
+            if N == 512 and prec == "f32":
+                kinds.append(("momentum", 0.05 * 5e-4 / 2.0 * N * N))
+            for kind, rr in kinds:
+                r = (rr,) * 3
+                pcode = ib.IB_FP32 if prec == "f32" else ib.IB_FP64
+                for _ in range(3):
+                    ib.ib_split_solve(pcode, 3, (N, N, N), r, f, psi)
+                torch.cuda.synchronize()
+                reps, tot = 10, 0.0
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    ib.ib_split_solve(pcode, 3, (N, N, N), r, f, psi)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    tot += e0.elapsed_time(e1)
+                ms = tot / reps
+                nbytes = 3 * 2 * f.element_size() * N ** 3
+                gbs = nbytes / (ms * 1e-3) / 1e9
+                rows.append({"n": N, "dtype": prec, "r": kind, "ms": round(ms, 5), "GB_per_s": round(gbs, 1),
+                             "frac": round(gbs / hbm, 4), "cell_updates_per_s": N ** 3 / (ms * 1e-3)})
+            del f, psi
+    return rows
+
+
 # --------------------------------------------------------------------------
 
 
@@ -224,6 +269,15 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    if args.line_solve_only:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        hbm, _ = peaks()
+        sizes = (args.n,) if args.n != 128 else (128, 256, 512)
+        rows = line_solve_leg(ib, torch, dev, flush, hbm, sizes=sizes,
+                              precisions=("f32",) if args.precision == "fp32" else ("f64",))
+        if rank == 0:
+            print(json.dumps({"metric": "line-solve HBM GB/s", "line_solve_table": rows}), flush=True)
+        return 0
     sc = scene(args)
     cells, nm, ne = sc.cells, sc.X.shape[0], sc.edges.shape[0]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 129 MB L2
@@ -324,28 +378,12 @@ def run_ours(args, rank, world, local):
             out["fp64"] = {"value": cells * world / (ms64 * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms64,
                            "steps_per_s": 1e3 / ms64 * world, "steps": k64,
                            "kernels_ms_per_launch": {k: round(v, 5) for k, v in p64.items()}}
-        # line-solve microbench: the paper's Poisson-comparison operator at 512^3
-        N = 512
-        f = torch.randn(N, N, N, dtype=torch.float32, device=dev)
-        psi = torch.empty_like(f)
-        r = (float(N * N),) * 3
-        for _ in range(3):
-            ib.ib_split_solve(ib.IB_FP32, 3, (N, N, N), r, f, psi)
-        torch.cuda.synchronize()
-        reps = 10
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            ib.ib_split_solve(ib.IB_FP32, 3, (N, N, N), r, f, psi)
-        e1.record()
-        torch.cuda.synchronize()
-        ms_ls = e0.elapsed_time(e1) / reps
-        ls_bytes = 3 * 2 * 4 * N ** 3
+        # line-solve microbench: the paper's Poisson-comparison problem
+        out["line_solve_table"] = line_solve_leg(ib, torch, dev, flush, hbm)
+        head = [r for r in out["line_solve_table"] if r["n"] == 512 and r["dtype"] == "f32" and r["r"] == "psi"][0]
         out["line_solve"] = {"workload": "(1-D_xx)(1-D_yy)(1-D_zz) psi = f, 512^3 FP32, r = N^2, 3 sweeps",
-                             "ms": ms_ls, "GB_per_s": ls_bytes / (ms_ls * 1e-3) / 1e9,
-                             "frac": ls_bytes / (ms_ls * 1e-3) / 1e9 / hbm,
-                             "cell_updates_per_s": N ** 3 / (ms_ls * 1e-3)}
-        del f, psi
+                             "ms": head["ms"], "GB_per_s": head["GB_per_s"], "frac": head["frac"],
+                             "cell_updates_per_s": head["cell_updates_per_s"]}
         # batched ensemble: 48 independent runs (N in {48, 64, 96, 128}, sigma
         # log-uniform in [0.1, 10], mu uniform in [0.01, 0.1]), one graph
         # launch per ensemble step, against the same members stepped one by one
