@@ -20,12 +20,12 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
   const int nx = a.n[0], ny = a.n[1], nz = DIM == 3 ? a.n[2] : 1;
   const long long cells = (long long)nx * ny * nz;
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells;
-       o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % nx);
-    const long long tq = o / nx;
-    const int j = (int)(tq % ny);
-    const int k = (int)(tq / ny);
+  // cell counts stay below 2^31 (n <= 512 per axis): 32-bit index arithmetic
+  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < (unsigned)cells; o += gridDim.x * blockDim.x) {
+    const int i = (int)(o % (unsigned)nx);
+    const unsigned tq = o / (unsigned)nx;
+    const int j = (int)(tq % (unsigned)ny);
+    const int k = (int)(tq / (unsigned)ny);
     long long dp[3], dm[3];
     dp[0] = i + 1 == nx ? 1 - nx : 1;
     dm[0] = i == 0 ? nx - 1 : -1;
@@ -59,22 +59,31 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
       nold[c] = a.first ? T(0) : a.Nold[c][o];
       pm[c] = a.first ? T(0) : a.p[o + dm[c]] + (a.psi ? a.psi[o + dm[c]] : T(0));
     }
+    // per axis: 1/2 (A+ u(+a) - A- u(-a)) / h_a with A+- the averages of two
+    // velocities is (1 / (4 h_a)) ((a0 + a1) u(+a) - (b0 + b1) u(-a)); the
+    // Laplacian sums (u(+a) + u(-a)) / h_a^2 and subtracts 2 u sum_a 1/h_a^2
+    T q4[DIM], s2 = T(0);
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      q4[ax] = T(0.25) * a.inv_h[ax];
+      s2 += a.inv_h2[ax];
+    }
     T R[DIM], Nn[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      T lap = T(0), adv = T(0);
+      T lap = T(-2) * s2 * uc[c], adv = T(0);
 #pragma unroll
       for (int ax = 0; ax < DIM; ++ax) {
-        lap += (up[c][ax] - T(2) * uc[c] + um[c][ax]) * a.inv_h2[ax];
-        T Ap, Am;
+        lap = fma(up[c][ax] + um[c][ax], a.inv_h2[ax], lap);
+        T sp, sm;
         if (ax == c) {
-          Ap = T(0.5) * (uc[c] + up[c][ax]);
-          Am = T(0.5) * (um[c][ax] + uc[c]);
+          sp = uc[c] + up[c][ax];
+          sm = um[c][ax] + uc[c];
         } else {
-          Ap = T(0.5) * (up[ax][ax] + ux[c][ax]);   // u_a at +e_a and at +e_a - e_c
-          Am = T(0.5) * (uc[ax] + um[ax][c]);       // u_a at the face and at -e_c
+          sp = up[ax][ax] + ux[c][ax];   // u_a at +e_a and at +e_a - e_c
+          sm = uc[ax] + um[ax][c];       // u_a at the face and at -e_c
         }
-        adv += T(0.5) * (Ap * up[c][ax] - Am * um[c][ax]) * a.inv_h[ax];
+        adv = fma(q4[ax], sp * up[c][ax] - sm * um[c][ax], adv);
       }
       const T gp = (p0 - pm[c]) * a.inv_h[c];
       const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[c];
@@ -162,24 +171,31 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
 #pragma unroll
     for (int e = 0; e < 4; ++e) nold[e] = P0[e] = Pm[e] = T(0);
   }
+  // the arithmetic of k_rhs
+  T q4[DIM], s2 = T(0);
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    q4[ax] = T(0.25) * a.inv_h[ax];
+    s2 += a.inv_h2[ax];
+  }
   T Rv[4], Nn[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const T u0 = S[0][e];
-    T lap = T(0), adv = T(0);
+    T lap = T(-2) * s2 * u0, adv = T(0);
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
       const T up = S[1 + 2 * ax][e], um = S[2 + 2 * ax][e];
-      lap += (up - T(2) * u0 + um) * a.inv_h2[ax];
-      T Ap, Am;
+      lap = fma(up + um, a.inv_h2[ax], lap);
+      T sp, sm;
       if (ax == C) {
-        Ap = T(0.5) * (u0 + up);
-        Am = T(0.5) * (um + u0);
+        sp = u0 + up;
+        sm = um + u0;
       } else {
-        Ap = T(0.5) * (Up[ax][e] + Ux[ax][e]);
-        Am = T(0.5) * (U0[ax][e] + Um[ax][e]);
+        sp = Up[ax][e] + Ux[ax][e];
+        sm = U0[ax][e] + Um[ax][e];
       }
-      adv += T(0.5) * (Ap * up - Am * um) * a.inv_h[ax];
+      adv = fma(q4[ax], sp * up - sm * um, adv);
     }
     const T gp = (P0[e] - Pm[e]) * a.inv_h[C];
     const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[e];
@@ -324,13 +340,15 @@ static inline unsigned grid_stride_blocks(long long work) {
 
 template <typename T>
 cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s) {
-  if (sizeof(T) == 4 && (a.n[0] & 3) == 0) {  // FP64 keeps the scalar kernel (register pressure)
-    const dim3 blk(32, 8);
-    const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)((a.n[1] + 7) / 8),
-                    (unsigned)((dim == 3 ? a.n[2] : 1) * dim));
-    if (dim == 2) k_rhs4<T, 2><<<grid, blk, 0, s>>>(a);
-    else k_rhs4<T, 3><<<grid, blk, 0, s>>>(a);
-    return cudaGetLastError();
+  if constexpr (sizeof(T) == 4) {  // FP64 keeps the scalar kernel (register pressure)
+    if ((a.n[0] & 3) == 0) {
+      const dim3 blk(32, 8);
+      const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)((a.n[1] + 7) / 8),
+                      (unsigned)((dim == 3 ? a.n[2] : 1) * dim));
+      if (dim == 2) k_rhs4<T, 2><<<grid, blk, 0, s>>>(a);
+      else k_rhs4<T, 3><<<grid, blk, 0, s>>>(a);
+      return cudaGetLastError();
+    }
   }
   const long long cells = (long long)a.n[0] * a.n[1] * (dim == 3 ? a.n[2] : 1);
   const unsigned g = grid_stride_blocks(cells);
