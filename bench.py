@@ -240,8 +240,10 @@ def run_reference(args, rank, world):
     sc = scene(args)
     P = O.params(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
     sim = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
-    steps = max(1, min(args.steps, 2))   # each oracle step takes ~10 s on one core
-    warm = min(args.warmup, 0)
+    # each oracle step takes about 2 s at 128^3 on one core: one untimed step
+    # (the first step takes the n = 0 branch) and at most 5 timed ones
+    steps = max(1, min(args.steps, 5))
+    warm = min(args.warmup, 1)
     sim.step(warm)
     t0 = time.perf_counter()
     sim.step(steps)
