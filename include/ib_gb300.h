@@ -270,6 +270,38 @@ const char *ib_kernel_name(int slot);
 int ib_adjoint_run(ib_grid_t g, int n_steps, int checkpoint_every, const double *X_target, double *loss,
                    double *dkappa);
 
+/* Checkpoint / resume (the paper has none): the complete state S^n of a grid
+ * -- u, p^{n-1/2}, psi^{n-1/2}, N(u^{n-1}), D.u^n, the marker positions X^n,
+ * U^{n-1} and the step count n -- as a host byte image, so that a grid
+ * loaded from it continues exactly as the saved one would (Sec. 3.4: the
+ * step reads nothing else).  Layout: a 64-byte header (magic "IBGMSTAT",
+ * version, dim, n[3], precision, scheme, marker and connection counts, n),
+ * the fields u[0..dim), p, psi, N[0..dim), D.u, each n0 n1 n2 elements of the
+ * grid's precision in grid order, X as [n_markers][dim] FP64 and U^{n-1} as
+ * [n_markers][dim] of the field precision, markers in the caller's order.
+ *   ib_state_size: bytes of the image.
+ *   ib_save_state: writes the image to host memory dst (bytes must match);
+ *     synchronises the grid's stream.
+ *   ib_load_state: replaces the grid's state by the image at host memory src.
+ *     The grid must have the same dim, n, precision, scheme and the same
+ *     structures added (marker and connection counts are checked; the
+ *     connections themselves are the caller's to match).
+ * Errors: IB_ERR_ARG (null pointer, size, image of another grid), IB_ERR_CUDA. */
+int ib_state_size(ib_grid_t g, size_t *bytes);
+int ib_save_state(ib_grid_t g, void *dst, size_t bytes);
+int ib_load_state(ib_grid_t g, const void *src, size_t bytes);
+
+/* Self-test of the bounded device waits (no counterpart in the paper).  The
+ * kernels that stage data with bulk tensor copies wait on mbarriers for at
+ * most 1 s; when a wait runs out they set a process-wide flag, which
+ * ib_diagnostics reports as IB_ERR_TIMEOUT, and return.  This call launches
+ * one CTA that arms an mbarrier for bytes no copy will deliver and waits with
+ * a 1 ms limit, so the wait runs out: *timed_out receives the flag (1 when the
+ * mechanism works), which is then cleared.  The CUDA context stays usable.
+ * Synchronises `stream` (a cudaStream_t; NULL: default stream).
+ * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+int ib_selftest_wait_timeout(void *stream, int *timed_out);
+
 #ifdef __cplusplus
 }
 #endif

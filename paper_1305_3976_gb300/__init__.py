@@ -28,7 +28,8 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
            "ib_set_markers", "ib_diagnostics", "ib_destroy_grid", "ib_error_string", "ib_last_error",
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
            "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
-           "ib_sweep_config", "ib_fix_sweep_config", "ib_adjoint_run")
+           "ib_sweep_config", "ib_fix_sweep_config", "ib_adjoint_run", "ib_selftest_wait_timeout",
+           "ib_state_size", "ib_save_state", "ib_load_state")
 
 
 class ib_grid_desc(C.Structure):
@@ -80,6 +81,10 @@ def lib():
         L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.ib_fix_sweep_config.argtypes = [vp, C.c_int, C.c_int]
         L.ib_adjoint_run.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp]
+        L.ib_selftest_wait_timeout.argtypes = [vp, C.POINTER(C.c_int)]
+        L.ib_state_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.ib_save_state.argtypes = [vp, vp, C.c_size_t]
+        L.ib_load_state.argtypes = [vp, vp, C.c_size_t]
         L.ib_kernel_name.argtypes = [C.c_int]
         L.ib_kernel_name.restype = C.c_char_p
         for name in EXPORTS:
@@ -200,6 +205,28 @@ def ib_diagnostics(g, check=True):
 
 def ib_destroy_grid(g):
     _check(lib().ib_destroy_grid(g), "ib_destroy_grid")
+
+
+def ib_save_state(g):
+    """The grid's state S^n as a bytes object (see include/ib_gb300.h)."""
+    n = C.c_size_t()
+    _check(lib().ib_state_size(g, C.byref(n)), "ib_state_size")
+    buf = (C.c_char * n.value)()
+    _check(lib().ib_save_state(g, buf, n.value), "ib_save_state")
+    return bytes(buf)
+
+
+def ib_load_state(g, image):
+    buf = C.create_string_buffer(bytes(image), len(image))
+    _check(lib().ib_load_state(g, buf, len(image)), "ib_load_state")
+
+
+def ib_selftest_wait_timeout(stream="current"):
+    """1 if a device wait that cannot complete ran out and was reported."""
+    flag = C.c_int(-1)
+    s = _current_stream() if stream == "current" else stream
+    _check(lib().ib_selftest_wait_timeout(C.c_void_p(s), C.byref(flag)), "ib_selftest_wait_timeout")
+    return flag.value
 
 
 def ib_adjoint_run(g, n_steps, checkpoint_every, X_target, n_edges):
@@ -341,6 +368,12 @@ class Grid:
     def adjoint(self, n_steps, X_target, checkpoint_every=20):
         """Advance n_steps; return (sum |X - X_target|^2, d loss / d kappa per connection)."""
         return ib_adjoint_run(self.h, n_steps, checkpoint_every, X_target, self.n_edges)
+
+    def save_state(self):
+        return ib_save_state(self.h)
+
+    def load_state(self, image):
+        ib_load_state(self.h, image)
 
     def sweep_configs(self):
         """Autotuned line-solve configuration per axis: (id, a, b, c)."""

@@ -114,6 +114,8 @@ cudaError_t launch_sweep_tma(int axis, int nfields, const SweepArgs<float> &a, c
 // process-wide flag set by a kernel whose bounded wait ran out; returns its
 // value and clears it
 int take_wait_timeout();
+// a kernel whose mbarrier wait cannot complete and runs out after limit_ns
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t s);
 
 // adjoint step (see ib_adjoint.cu)
 template <typename T>

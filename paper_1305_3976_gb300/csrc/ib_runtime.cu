@@ -1212,6 +1212,153 @@ int ib_cyclic_solve_lines(int precision, int dim, const int n[3], int axis, doub
   return IB_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the state S^n as a host byte image.
+//   header | fields u[d], p, psi, Nold[d], div (n0 n1 n2 elements each, field
+//   precision, grid order) | X [nm][d] FP64 | U^{n-1} [nm][d] field precision
+//   (markers in the caller's order)
+
+namespace {
+
+struct StateHeader {
+  char magic[8];  // "IBGMSTAT"
+  int32_t version, dim, n[3], precision, scheme;
+  int64_t nm, ne, step;
+};
+static_assert(sizeof(StateHeader) == 64, "the state image header is 64 bytes");
+
+// the field part of the image: u[0..d), p, psi, Nold[0..d), div
+int state_fields(ib_grid_s *g, void *out[9]) {
+  int k = 0;
+  for (int a = 0; a < g->dim; ++a) out[k++] = g->u[a];
+  out[k++] = g->p;
+  out[k++] = g->psi;
+  for (int a = 0; a < g->dim; ++a) out[k++] = g->Nold[a];
+  out[k++] = g->div;
+  return k;
+}
+
+size_t state_bytes(const ib_grid_s *g) {
+  return sizeof(StateHeader) + g->esz * (size_t)g->cells * (2 * g->dim + 3) +
+         (sizeof(double) + g->esz) * (size_t)g->nm * g->dim;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ib_state_size(ib_grid_t g, size_t *bytes) {
+  if (!g || !bytes) return fail(IB_ERR_ARG, "null argument");
+  *bytes = state_bytes(g);
+  return IB_OK;
+}
+
+int ib_save_state(ib_grid_t g, void *dst, size_t bytes) {
+  if (!g || !dst) return fail(IB_ERR_ARG, "null argument");
+  if (bytes != state_bytes(g)) return fail(IB_ERR_ARG, "bytes = %zu, the state needs %zu", bytes, state_bytes(g));
+  int rc = enter(g);
+  if (!rc) rc = prepare(g);
+  if (rc) return rc;
+  const int d = g->dim;
+  const int64_t nm = g->nm;
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "IBGMSTAT", 8);
+  h.version = 1;
+  h.dim = d;
+  for (int a = 0; a < 3; ++a) h.n[a] = g->n[a];
+  h.precision = g->prec;
+  h.scheme = g->desc.scheme;
+  h.nm = nm;
+  h.ne = g->ne;
+  h.step = g->step;
+  char *o = (char *)dst;
+  memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  const size_t fb = g->esz * (size_t)g->cells;
+  void *fields[9];
+  const int nf = state_fields(g, fields);
+  for (int i = 0; i < nf; ++i) {
+    IB_CUDA(cudaMemcpyAsync(o, fields[i], fb, cudaMemcpyDeviceToHost, g->s));
+    o += fb;
+  }
+  if (nm) {
+    IB_CUDA(launch_markers_layout(g->stage, g->X, g->perm, nm, d, 0, g->s));
+    IB_CUDA(cudaMemcpyAsync(o, g->stage, sizeof(double) * nm * d, cudaMemcpyDeviceToHost, g->s));
+    o += sizeof(double) * nm * d;
+    std::vector<char> uold(g->esz * nm * d);
+    std::vector<int32_t> perm(nm);
+    IB_CUDA(cudaMemcpyAsync(uold.data(), g->Uold[0], uold.size(), cudaMemcpyDeviceToHost, g->s));
+    IB_CUDA(cudaMemcpyAsync(perm.data(), g->perm, sizeof(int32_t) * nm, cudaMemcpyDeviceToHost, g->s));
+    IB_CUDA(cudaStreamSynchronize(g->s));
+    for (int64_t k = 0; k < nm; ++k)
+      for (int a = 0; a < d; ++a)
+        memcpy(o + g->esz * ((int64_t)perm[k] * d + a), uold.data() + g->esz * (a * nm + k), g->esz);
+  }
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  return leave(g);
+}
+
+int ib_load_state(ib_grid_t g, const void *src, size_t bytes) {
+  if (!g || !src) return fail(IB_ERR_ARG, "null argument");
+  if (bytes != state_bytes(g)) return fail(IB_ERR_ARG, "bytes = %zu, the state needs %zu", bytes, state_bytes(g));
+  StateHeader h;
+  memcpy(&h, src, sizeof(h));
+  if (memcmp(h.magic, "IBGMSTAT", 8) != 0 || h.version != 1) return fail(IB_ERR_ARG, "not a saved state");
+  if (h.dim != g->dim || h.n[0] != g->n[0] || h.n[1] != g->n[1] || h.n[2] != g->n[2] || h.precision != g->prec ||
+      h.nm != g->nm || h.ne != g->ne || h.scheme != g->desc.scheme || h.step < 0)
+    return fail(IB_ERR_ARG, "the saved state belongs to a grid of another shape, precision, scheme or structure");
+  int rc = enter(g);
+  if (!rc) rc = prepare(g);
+  if (rc) return rc;
+  const int d = g->dim;
+  const int64_t nm = g->nm;
+  const char *o = (const char *)src + sizeof(h);
+  const size_t fb = g->esz * (size_t)g->cells;
+  void *fields[9];
+  const int nf = state_fields(g, fields);
+  for (int i = 0; i < nf; ++i) {
+    IB_CUDA(cudaMemcpyAsync(fields[i], o, fb, cudaMemcpyHostToDevice, g->s));
+    o += fb;
+  }
+  std::vector<char> uold;
+  if (nm) {
+    IB_CUDA(cudaMemcpyAsync(g->stage, o, sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(launch_markers_layout(g->stage, g->X, g->perm, nm, d, 1, g->s));
+    o += sizeof(double) * nm * d;
+    std::vector<int32_t> perm(nm);
+    IB_CUDA(cudaMemcpyAsync(perm.data(), g->perm, sizeof(int32_t) * nm, cudaMemcpyDeviceToHost, g->s));
+    IB_CUDA(cudaStreamSynchronize(g->s));
+    uold.resize(g->esz * nm * d);
+    for (int64_t k = 0; k < nm; ++k)
+      for (int a = 0; a < d; ++a)
+        memcpy(uold.data() + g->esz * (a * nm + k), o + g->esz * ((int64_t)perm[k] * d + a), g->esz);
+    IB_CUDA(cudaMemcpyAsync(g->Uold[0], uold.data(), uold.size(), cudaMemcpyHostToDevice, g->s));
+  }
+  g->step = h.step;
+  g->div_valid = true;
+  g->loc_valid = false;
+  if ((rc = ensure_loc(g))) return rc;
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  return leave(g);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int ib_selftest_wait_timeout(void *stream, int *timed_out) {
+  if (!timed_out) return fail(IB_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  take_wait_timeout();  // start from a clear flag
+  IB_CUDA(launch_wait_selftest(1000000ull, s));  // 1 ms
+  IB_CUDA(cudaStreamSynchronize(s));
+  *timed_out = take_wait_timeout();
+  return IB_OK;
+}
+
 int ib_split_solve(int precision, int dim, const int n[3], const double r[3], const void *f, void *psi,
                    void *stream) {
   if (!r) return fail(IB_ERR_ARG, "null r");

@@ -29,7 +29,7 @@ namespace ibg {
 namespace {
 
 constexpr int kStages = 3;
-constexpr long long kSpin = 1LL << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 __device__ int g_wait_timeout = 0;
 
@@ -53,10 +53,17 @@ __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
                : "memory");
   return done != 0;
 }
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
-  for (long long i = 0; i < kSpin; ++i)
-    if (bar_try(b, parity)) return true;
-  return false;
+__device__ __forceinline__ unsigned long long gtime_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase with the given parity, at most limit_ns nanoseconds
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, unsigned long long limit_ns = kWaitNs) {
+  const unsigned long long t0 = gtime_ns();
+  while (!bar_try(b, parity))
+    if (gtime_ns() - t0 > limit_ns) return false;
+  return true;
 }
 __device__ __forceinline__ void tma_in(float *dst, const CUtensorMap *m, int x, int y, int z, uint64_t *b) {
   asm volatile(
@@ -275,6 +282,22 @@ void sweep_tma_shape(int nl, int *ch, int *w) {
   const TmaShape t = tma_shape(nl);
   *ch = t.ch;
   *w = t.w;
+}
+
+// One CTA arms an mbarrier for 16 bytes that no copy will deliver and waits
+// for it with a limit of limit_ns: the wait runs out and sets the flag.
+__global__ void k_wait_selftest(unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  bar_init(&bar);
+  bar_init_fence();
+  bar_expect(&bar, 16);
+  if (!bar_wait(&bar, 0, limit_ns)) atomicExch(&g_wait_timeout, 1);
+}
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_ns);
+  return cudaGetLastError();
 }
 
 int take_wait_timeout() {
