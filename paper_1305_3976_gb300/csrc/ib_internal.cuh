@@ -7,6 +7,31 @@
 
 namespace ibg {
 
+// Programmatic dependent launch.  The step's kernels are launched with
+// launch_pdl, so a kernel's CTAs can be scheduled while the previous kernel of
+// the stream drains; every such kernel calls pdl_wait() before its first
+// global memory access (it returns once the previous kernel has completed and
+// its writes are visible; without the launch attribute it returns at once)
+// and pdl_release() to let the next kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // 4 contiguous elements at p (16-byte aligned for float, 32 for double)
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4 *>(p);

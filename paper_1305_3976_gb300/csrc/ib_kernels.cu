@@ -18,6 +18,8 @@ namespace ibg {
 // a cell above and below the c-face) add up to 1/2 (A+ u_c(+a) - A- u_c(-a))/h_a.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
+  pdl_wait();
+  pdl_release();
   const int nx = a.n[0], ny = a.n[1], nz = DIM == 3 ? a.n[2] : 1;
   const long long cells = (long long)nx * ny * nz;
   // cell counts stay below 2^31 (n <= 512 per axis): 32-bit index arithmetic
@@ -211,6 +213,8 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
 // (x/4, y, z * d + c) launch grid.  The arithmetic per cell is the one above.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_rhs4(const RhsArgs<T> a) {
+  pdl_wait();
+  pdl_release();
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z / DIM, c = blockIdx.z - (blockIdx.z / DIM) * DIM;
@@ -345,16 +349,14 @@ cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s) {
       const dim3 blk(32, 8);
       const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)((a.n[1] + 7) / 8),
                       (unsigned)((dim == 3 ? a.n[2] : 1) * dim));
-      if (dim == 2) k_rhs4<T, 2><<<grid, blk, 0, s>>>(a);
-      else k_rhs4<T, 3><<<grid, blk, 0, s>>>(a);
-      return cudaGetLastError();
+      if (dim == 2) return launch_pdl(k_rhs4<T, 2>, grid, blk, 0, s, a);
+      return launch_pdl(k_rhs4<T, 3>, grid, blk, 0, s, a);
     }
   }
   const long long cells = (long long)a.n[0] * a.n[1] * (dim == 3 ? a.n[2] : 1);
   const unsigned g = grid_stride_blocks(cells);
-  if (dim == 2) k_rhs<T, 2><<<g, 256, 0, s>>>(a);
-  else k_rhs<T, 3><<<g, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (dim == 2) return launch_pdl(k_rhs<T, 2>, dim3(g), dim3(256), 0, s, a);
+  return launch_pdl(k_rhs<T, 3>, dim3(g), dim3(256), 0, s, a);
 }
 
 template <typename T>

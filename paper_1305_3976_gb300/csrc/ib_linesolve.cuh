@@ -402,6 +402,8 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
 
 template <typename T, int R, int PRO, int EPI, bool FULL>
 __global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
+  pdl_wait();
+  pdl_release();
   const int lane = threadIdx.x & 31;
   const int nx = a.n[0], ny = a.n[1];
   const long long nlines = (long long)ny * (a.dim == 3 ? a.n[2] : 1);
@@ -425,6 +427,8 @@ __global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
 // elements per field).
 template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL>
 __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const int axis) {
+  pdl_wait();
+  pdl_release();
   __shared__ T sz[W][VW][33];
   __shared__ T lp[CH + 1];  // lam^0 .. lam^CH
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -657,12 +661,13 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
     const long long ctas = (nlines + 7) / 8;
     const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
     dim3 grid((unsigned)(ctas < cap ? ctas : cap), nfields);  // warps loop over lines
-    if (nl == 128) k_sweep_x<T, 1, PRO, EPI, true><<<grid, 256, 0, s>>>(a);
-    else if (nl < 128) k_sweep_x<T, 1, PRO, EPI, false><<<grid, 256, 0, s>>>(a);
-    else if (nl == 256) k_sweep_x<T, 2, PRO, EPI, true><<<grid, 256, 0, s>>>(a);
-    else if (nl < 256) k_sweep_x<T, 2, PRO, EPI, false><<<grid, 256, 0, s>>>(a);
-    else if (nl == 512) k_sweep_x<T, 4, PRO, EPI, true><<<grid, 256, 0, s>>>(a);
-    else k_sweep_x<T, 4, PRO, EPI, false><<<grid, 256, 0, s>>>(a);
+    const dim3 b(256);
+    if (nl == 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, true>, grid, b, 0, s, a);
+    if (nl < 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, false>, grid, b, 0, s, a);
+    if (nl == 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, true>, grid, b, 0, s, a);
+    if (nl < 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, false>, grid, b, 0, s, a);
+    if (nl == 512) return launch_pdl(k_sweep_x<T, 4, PRO, EPI, true>, grid, b, 0, s, a);
+    return launch_pdl(k_sweep_x<T, 4, PRO, EPI, false>, grid, b, 0, s, a);
   } else {
     const int other = axis == 1 ? (a.dim == 3 ? a.n[2] : 1) : a.n[1];
     const int nx = a.n[0];
@@ -674,9 +679,9 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
   case I: {                                                                                             \
     constexpr StridedCfg c = strided_cfg(I);                                                            \
     if (nl == c.ch * c.w)                                                                               \
-      k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true><<<grid(c.vw), 32 * c.w, 0, s>>>(a, axis);          \
-    else k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false><<<grid(c.vw), 32 * c.w, 0, s>>>(a, axis);      \
-  } break;
+      return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
+    return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
+  }
     if constexpr (sizeof(T) == 8) {
       switch (cfg) { IBG_S(0) IBG_S(3) IBG_S(6) IBG_S(8) IBG_S(10) default: return cudaErrorInvalidValue; }
     } else if constexpr (PRO == PRO_DIV) {

@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(256) k_locate(const MarkerArgs m, double *cons
 // (interpolation, next step).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
+  pdl_wait();
+  pdl_release();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned k = t / DIM;
   const int c = (int)(t - k * DIM);
@@ -214,6 +216,8 @@ __device__ __forceinline__ void row4_add(double *r, int xs, int nx, const double
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
                                                 const T *const u2) {
+  pdl_wait();
+  pdl_release();
   StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w);
   T s = T(0);
   if (L.valid) {
@@ -240,6 +244,8 @@ __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *con
 //     accuracy as rounding the FP64 difference to FP32.
 template <typename T, int DIM, bool FRAC>
 __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
+  pdl_wait();
+  pdl_release();
   const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned a = gt >> 3;
   const int lane8 = (int)(gt & 7);
@@ -310,6 +316,8 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
 // their initial positions, so neighbouring groups update neighbouring nodes.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
+  pdl_wait();
+  pdl_release();
   StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w);
   if (!L.valid) return;
   T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
@@ -354,16 +362,16 @@ template <typename T>
 cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
   const unsigned g = nblocks(m.nm * m.dim * (m.dim == 3 ? 16 : 4), 256);
-  if (m.dim == 2) k_interp<T, 2><<<g, 256, 0, s>>>(m, u[0], u[1], u[1]);
-  else k_interp<T, 3><<<g, 256, 0, s>>>(m, u[0], u[1], u[2]);
+  if (m.dim == 2) return launch_pdl(k_interp<T, 2>, dim3(g), dim3(256), 0, s, m, u[0], u[1], u[1]);
+  return launch_pdl(k_interp<T, 3>, dim3(g), dim3(256), 0, s, m, u[0], u[1], u[2]);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_update(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
-  if (m.dim == 2) k_update<T, 2><<<nblocks(m.nm * 2, 256), 256, 0, s>>>(m);
-  else k_update<T, 3><<<nblocks(m.nm * 3, 256), 256, 0, s>>>(m);
+  if (m.dim == 2) return launch_pdl(k_update<T, 2>, dim3(nblocks(m.nm * 2, 256)), dim3(256), 0, s, m);
+  return launch_pdl(k_update<T, 3>, dim3(nblocks(m.nm * 3, 256)), dim3(256), 0, s, m);
   return cudaGetLastError();
 }
 
@@ -372,11 +380,11 @@ cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
   const unsigned g = nblocks(m.nm * 8, 256);
   if (m.frac_force) {
-    if (m.dim == 2) k_force<T, 2, true><<<g, 256, 0, s>>>(m);
-    else k_force<T, 3, true><<<g, 256, 0, s>>>(m);
+    if (m.dim == 2) return launch_pdl(k_force<T, 2, true>, dim3(g), dim3(256), 0, s, m);
+    return launch_pdl(k_force<T, 3, true>, dim3(g), dim3(256), 0, s, m);
   } else {
-    if (m.dim == 2) k_force<T, 2, false><<<g, 256, 0, s>>>(m);
-    else k_force<T, 3, false><<<g, 256, 0, s>>>(m);
+    if (m.dim == 2) return launch_pdl(k_force<T, 2, false>, dim3(g), dim3(256), 0, s, m);
+    return launch_pdl(k_force<T, 3, false>, dim3(g), dim3(256), 0, s, m);
   }
   return cudaGetLastError();
 }
@@ -385,8 +393,8 @@ template <typename T>
 cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
   const unsigned g = nblocks(m.nm * m.dim * (m.dim == 3 ? 16 : 4), 256);
-  if (m.dim == 2) k_spread<T, 2><<<g, 256, 0, s>>>(m, f[0], f[1], f[1]);
-  else k_spread<T, 3><<<g, 256, 0, s>>>(m, f[0], f[1], f[2]);
+  if (m.dim == 2) return launch_pdl(k_spread<T, 2>, dim3(g), dim3(256), 0, s, m, f[0], f[1], f[1]);
+  return launch_pdl(k_spread<T, 3>, dim3(g), dim3(256), 0, s, m, f[0], f[1], f[2]);
   return cudaGetLastError();
 }
 

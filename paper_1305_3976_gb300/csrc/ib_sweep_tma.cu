@@ -92,6 +92,8 @@ template <int CH, int W, bool FULL>
 __global__ void __launch_bounds__(32 * W, 1) k_sweep_tma(const __grid_constant__ SweepTmaMaps maps,
                                                          const SweepArgs<float> a, const int axis, const int nbox,
                                                          const int boxlen) {
+  pdl_wait();
+  pdl_release();
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float sz[W][33];
   __shared__ float lp[CH + 1];  // lam^0 .. lam^CH
@@ -337,8 +339,7 @@ cudaError_t launch_sweep_tma(int axis, int nfields, const SweepArgs<float> &a, c
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int ctas = nslab < sms * per_sm ? nslab : sms * per_sm;
-    kernel<<<ctas, threads, smem, s>>>(maps, a, axis, nbox, boxlen);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(ctas), dim3(threads), smem, s, maps, a, axis, nbox, boxlen);
   };
   const TmaShape t = tma_shape(nl);
   const bool full = t.ch * t.w == nl;
