@@ -86,3 +86,27 @@ def rate(r1, r2, r4, fibers=1, thick=False):
     den = np.sqrt(w2 * np.sum((r2["X"] - coarse_markers(r4["X"], 2 * f2 if thick else fibers, thick)) ** 2))
     out["X"] = float(np.log2(num / den))
     return out
+
+
+def thin_ellipse_area_history(N, dt, t_end=4.0, t_fit=2.0, sample=0.05, precision="fp64"):
+    """Relative area loss (A0 - A(t)) / A0 of the thin ellipse (sigma = 1,
+    Sec. 5.1) sampled every `sample` time units from t_fit to t_end, and the
+    final marker positions.  A is the area enclosed by the fiber (signed
+    shoelace sum over its connections, ib_diagnostics), A0 = pi r1 r2."""
+    r1, r2 = 5 / 28, 7 / 20
+    sc = I.thin_ellipse_2d(n=N, ns=19 * N // 4, r1=r1, r2=r2, mu=0.01, dt=dt, kernel="peskin4", sigma=1.0)
+    g = ib.Grid(2, sc.n, rho=sc.rho, mu=sc.mu, dt=dt, precision=precision, kernel="peskin4", rotate_split=True)
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest)
+    A0 = np.pi * r1 * r2
+    total, chunk = int(round(t_end / dt)), int(round(sample / dt))
+    ts, loss = [], []
+    done = 0
+    while done < total:
+        g.step(chunk)
+        done += chunk
+        if done * dt >= t_fit - 1e-9:
+            ts.append(done * dt)
+            loss.append((A0 - g.diagnostics()["volume"]) / A0)
+    X = g.markers()
+    g.close()
+    return np.array(ts), np.array(loss), X
