@@ -4,13 +4,16 @@ FP64 fields: the GPU and the oracle evaluate the same algorithm with different
 summation orders (atomics in spreading, CSR vs edge-order force sums, the
 two-factor recurrence vs the Schur solve) and a different but equivalent
 Douglas form (increment form, Sec. 3.4 Steps 3c-3d).  The psi operator has
-condition number up to 1 + 4 N^2, so two correct FP64 evaluations differ by up
-to ~ (1 + 4 N^2) n eps norm-wise in p and psi per step; u and X inherit a
-smaller share through the gradient.  The test uses norm-wise relative errors
-with that bound.
+condition number up to 1 + 4 N^2, so two correct FP64 evaluations may differ
+by up to ~ (1 + 4 N^2) n eps norm-wise in p and psi per step (psi_bound); u
+and X inherit a smaller share through the gradient.  The stated target is
+tighter: u and p within 1e-12 relative (norm-wise) per step, markers 1e-13
+absolute; measured at most 4.6e-14 (u), 3.5e-13 (p, 128^3) and 3.3e-16 (X).
+psi, an increment near zero, is held to psi_bound (measured 3.9e-12 after two
+128^3 steps).
 
-FP32 fields (FP64 markers): errors against the FP64 oracle are measured and
-must stay within the bounds stated in the test.
+FP32 fields (FP64 markers): within 1e-5 relative velocity and 1e-6 h marker
+error after the 100 steps of the 2D workload (measured 1.3e-7 and 5.5e-8 h).
 """
 import numpy as np
 import pytest
@@ -62,6 +65,14 @@ def psi_bound(sc, steps):
     return 64.0 * steps * N * EPS64 * (1 + 4.0 * N * N)
 
 
+def assert_fp64(e, steps):
+    """The FP64 targets: u and p 1e-12 relative per step, markers 1e-13
+    (absent for fluid-only runs); psi is checked against psi_bound."""
+    assert e["u"] <= 1e-12 * steps and e["p"] <= 1e-12 * steps, e
+    if "X" in e:
+        assert e["X"] < 1e-13, e
+
+
 @pytest.mark.parametrize("kernel", ["peskin4", "cos4"])
 @pytest.mark.parametrize("rotate", [True, False])
 def test_fp64_thin_ellipse_2d(kernel, rotate):
@@ -71,9 +82,8 @@ def test_fp64_thin_ellipse_2d(kernel, rotate):
         ora.step(steps)
         g.step(steps)
         e = compare(ora, g)
-        done = ora.n
-        assert e["u"] < psi_bound(sc, done) and e["p"] < psi_bound(sc, done), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
     g.close()
 
 
@@ -84,8 +94,8 @@ def test_fp64_ellipsoid_3d_small():
         ora.step(steps)
         g.step(steps)
         e = compare(ora, g)
-        assert e["u"] < psi_bound(sc, ora.n) and e["p"] < psi_bound(sc, ora.n), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
     g.close()
 
 
@@ -99,7 +109,8 @@ def test_fp64_ragged_anisotropic_fluid_only():
     ora.step(3)
     g.step(3)
     e = compare(ora, g)
-    assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
+    assert_fp64(e, 3)
+    assert e["psi"] < psi_bound(sc, 3), e
     g.close()
 
 
@@ -111,8 +122,8 @@ def test_fp64_full_size_ellipsoid_128_one_step():
     ora.step(2)
     g.step(2)
     e = compare(ora, g)
-    assert e["u"] < psi_bound(sc, 2) and e["p"] < psi_bound(sc, 2), e
-    assert e["X"] < 1e-13, e
+    assert_fp64(e, 2)
+    assert e["psi"] < psi_bound(sc, 2), e
     g.close()
 
 
@@ -124,8 +135,8 @@ def test_fp32_thin_ellipse_100_steps_error_vs_fp64_oracle():
     g.step(100)
     e = compare(ora, g)
     h = 1.0 / 64
-    assert e["u"] < 1e-4, e
-    assert e["X"] < 1e-4 * h, e
+    assert e["u"] < 1e-5, e
+    assert e["X"] < 1e-6 * h, e
     g.close()
 
 
