@@ -57,12 +57,14 @@ __device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
 // lam = 2r / (1 + 2r + sqrt(1 + 4r)) in [0, 1) and c = r / lam.  The inverse is
 // two first-order cyclic recurrences and a scale; each recurrence is a
 // non-periodic pass plus a rank-one periodic correction with weight
-// 1 / (1 - lam^n).
+// 1 / (1 - lam^n).  The scale is applied once, in the sweep's epilogue: a
+// chain of sweeps (each one linear) passes 1 in all sweeps but the last,
+// which carries the product of the chain's 1/c.
 template <typename T>
 struct LineCoef {
   const T *pw;  // lam^k for k = 0 .. n  (device)
   T lam;
-  T inv_c;      // 1 / c
+  T scale;      // factor applied to the solution: 1 / c for one complete solve
   T inv_1m;     // 1 / (1 - lam^n)
 };
 

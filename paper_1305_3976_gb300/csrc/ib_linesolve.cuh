@@ -108,14 +108,13 @@ __device__ __forceinline__ void stv(T *p, const T (&v)[VW]) {
 // warp and reused for every line it solves.
 template <typename T, int R>
 struct XLineCoef {
-  T lam, l2, l3, l4, inv_c, inv_1m;
+  T lam, l2, l3, l4, inv_1m;
   T gk[5];      // lam^(4 * 2^k)
   T gf, gb;     // gains of lanes 0..lane and lane..31
   T pf[R], pb[R];  // lam^(i0) and lam^(n - i0 - 4) of this lane's chunks
   __device__ __forceinline__ void load(const LineCoef<T> &co, int n, int lane) {
     const T *pw = co.pw;
     lam = co.lam;
-    inv_c = co.inv_c;
     inv_1m = co.inv_1m;
     l2 = ld_ro(pw + 2);
     l3 = ld_ro(pw + 3);
@@ -201,7 +200,7 @@ __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, in
       const T t = fma(ld_ro(pw + (n - i0 - len)), K, cin[r]);
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        if (e < len) v[r][e] = fma(ld_ro(pw + (len - e)), t, v[r][e]) * co.inv_c;
+        if (e < len) v[r][e] = fma(ld_ro(pw + (len - e)), t, v[r][e]);
     }
   }
 }
@@ -265,10 +264,10 @@ __device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, i
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const T t = fma(c.pb[r], K, cin[r]);
-    v[r][0] = fma(c.l4, t, v[r][0]) * c.inv_c;
-    v[r][1] = fma(c.l3, t, v[r][1]) * c.inv_c;
-    v[r][2] = fma(c.l2, t, v[r][2]) * c.inv_c;
-    v[r][3] = fma(lam, t, v[r][3]) * c.inv_c;
+    v[r][0] = fma(c.l4, t, v[r][0]);
+    v[r][1] = fma(c.l3, t, v[r][1]);
+    v[r][2] = fma(c.l2, t, v[r][2]);
+    v[r][3] = fma(lam, t, v[r][3]);
   }
 }
 
@@ -354,6 +353,15 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
   }
   if (FULL) solve_line_warp_full<T, R>(xc, lane, v);
   else solve_line_warp<T, R>(a.co, nx, lane, v);
+  // the scale 1/c (EPI_ADDU folds it into the sum); skipped in the unscaled
+  // sweeps of a chain
+  const T sc = a.co.scale;
+  if (EPI != EPI_ADDU && sc != T(1)) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[r][e] *= sc;
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i0 = (r * 32 + lane) * 4;
@@ -364,7 +372,7 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
         T uu[4];
         ld4(a.uo[comp] + base + i0, uu);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) uu[e] += v[r][e];
+        for (int e = 0; e < 4; ++e) uu[e] = fma(v[r][e], sc, uu[e]);
         st4(a.uo[comp] + base + i0, uu);
       }
     } else if (EPI == EPI_P && vec) {
@@ -390,7 +398,7 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
           if (EPI == EPI_STORE) {
             F[o] = v[r][e];
           } else if (EPI == EPI_ADDU) {
-            a.uo[comp][o] = old[e] + v[r][e];
+            a.uo[comp][o] = fma(v[r][e], sc, old[e]);
           } else {
             F[o] = v[r][e];
             a.p[o] = old[e] + v[r][e];
@@ -572,11 +580,20 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) {
           const int pe = FULL ? CH - e : max(0, len - e);
-          v[e][c] = fma(lp[pe], t, v[e][c]) * a.co.inv_c;
+          v[e][c] = fma(lp[pe], t, v[e][c]);
         }
     }
   }
   if (!xok) return;
+  // the scale 1/c (EPI_ADDU folds it into the sum); skipped in the unscaled
+  // sweeps of a chain
+  const T sc = a.co.scale;
+  if (EPI != EPI_ADDU && sc != T(1)) {
+#pragma unroll
+    for (int e = 0; e < CH; ++e)
+#pragma unroll
+      for (int c = 0; c < VW; ++c) v[e][c] *= sc;
+  }
   if (EPI == EPI_STORE) {
 #pragma unroll
     for (int e = 0; e < CH; ++e)
@@ -596,7 +613,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
         T old[VW];
         ldv<VW>(tgt + o0 + e * stride, old);
 #pragma unroll
-        for (int c = 0; c < VW; ++c) v[e][c] += old[c];
+        for (int c = 0; c < VW; ++c) v[e][c] = EPI == EPI_ADDU ? fma(v[e][c], sc, old[c]) : v[e][c] + old[c];
       }
 #pragma unroll
     for (int e = 0; e < CH; ++e)

@@ -108,7 +108,11 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
   k_fill_powers<<<dim, 128, 0, s>>>(base, nn[0], nn[1], nn[2], lam[0], lam[1], lam[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+  // the sweeps are linear: the last one applies the product of the 1/c
+  double prod = 1.0;
+  for (int a = 0; a < dim; ++a) prod *= inv_c[a];
   for (int a = 0; a < dim; ++a) {
+    const double scale = a == dim - 1 ? prod : 1.0;
     if (precision == IB_FP32) {
       SweepArgs<float> sa;
       memset(&sa, 0, sizeof(sa));
@@ -117,7 +121,7 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
       for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
       sa.dim = dim;
       sa.co = LineCoef<float>{reinterpret_cast<const float *>(base + (size_t)(3 + a) * kRow), (float)lam[a],
-                              (float)inv_c[a], (float)inv_1m[a]};
+                              (float)scale, (float)inv_1m[a]};
       e = launch_sweep<float>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
     } else {
       SweepArgs<double> sa;
@@ -126,7 +130,7 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
       sa.fin[0] = a == 0 ? (const double *)f : nullptr;
       for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
       sa.dim = dim;
-      sa.co = LineCoef<double>{base + (size_t)a * kRow, lam[a], inv_c[a], inv_1m[a]};
+      sa.co = LineCoef<double>{base + (size_t)a * kRow, lam[a], scale, inv_1m[a]};
       e = launch_sweep<double>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
     }
     if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));

@@ -102,6 +102,19 @@ const LineCoef<float> &coef_of<float>(const DevCoef &c) { return c.f; }
 template <>
 const LineCoef<double> &coef_of<double>(const DevCoef &c) { return c.d; }
 
+// Coefficients of sweep st of a chain of d sweeps over the operators co[ax]:
+// the sweeps are linear, so the chain applies the product of its 1/c once,
+// in the last sweep, and the others run unscaled.
+constexpr int kAxes[3] = {0, 1, 2};
+template <typename T>
+LineCoef<T> chain_coef(const DevCoef *co, const int *order, int st, int d) {
+  LineCoef<T> c = coef_of<T>(co[order[st]]);
+  double prod = 1.0;
+  for (int q = 0; q < d; ++q) prod *= co[order[q]].d.scale;
+  c.scale = st == d - 1 ? (T)prod : T(1);
+  return c;
+}
+
 // process-wide cache for the stand-alone line-solve entry points
 std::mutex g_cache_mu;
 std::map<std::tuple<int, int, double>, DevCoef> g_cache;  // (device, n, r)
@@ -285,7 +298,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   sa.dim = d;
   for (int st = 0; st < d; ++st) {
     const int ax = order[st];
-    sa.co = coef_of<T>(g->coef[0][ax]);
+    sa.co = chain_coef<T>(g->coef[0], order, st, d);
     const bool last = st == d - 1;
     IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, last ? EPI_ADDU : EPI_STORE, d, sa, g->s, last ? g->tune_r[ax] : g->tune[ax]));
     if ((rc = mark(6 + st))) return rc;
@@ -295,7 +308,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   sa.f[0] = sa.f[1] = sa.f[2] = (T *)g->psi;
   for (int st = 0; st < d; ++st) {
     const int ax = order[st];
-    sa.co = coef_of<T>(g->coef[1][ax]);
+    sa.co = chain_coef<T>(g->coef[1], order, st, d);
     const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
     const int epi = st == d - 1 ? EPI_P : EPI_STORE;
     const bool plain = pro == PRO_LOAD && epi == EPI_STORE;
@@ -800,14 +813,14 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
       IB_CUDA(adjoint_fields_a<T>(f, g->s));
       sa.f[0] = sa.f[1] = sa.f[2] = f.q;
       for (int ax = 0; ax < d; ++ax) {
-        sa.co = coef_of<T>(g->coef[1][ax]);
+        sa.co = chain_coef<T>(g->coef[1], kAxes, ax, d);
         IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, 1, sa, g->s, g->tune[ax]));
       }
       IB_CUDA(adjoint_fields_b<T>(f, g->s));
       // Steps 3c-3d: R_bar = M^{-1} u'_bar
       for (int a = 0; a < 3; ++a) sa.f[a] = f.rb[a];
       for (int ax = 0; ax < d; ++ax) {
-        sa.co = coef_of<T>(g->coef[0][ax]);
+        sa.co = chain_coef<T>(g->coef[0], kAxes, ax, d);
         IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, g->tune[ax]));
       }
       // Steps 3a-3b

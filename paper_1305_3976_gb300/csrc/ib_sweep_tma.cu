@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_sweep_tma(const __grid_constant__
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) {
           const int pe = FULL ? CH - e : max(0, len - e);
-          sl[(start + e) * 32 + lane] = fmaf(lp[pe], t, v[e]) * a.co.inv_c;
+          sl[(start + e) * 32 + lane] = fmaf(lp[pe], t, v[e]) * a.co.scale;
         }
     }
     proxy_fence();  // this thread's results before the copy-out reads them
