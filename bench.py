@@ -155,6 +155,15 @@ def kernel_bytes(name, cells, nm, ne, w, d=3):
     return m[name]
 
 
+STEP_SLOTS = ("interp", "update", "force", "rhs", "spread", "mom_sweep_1", "mom_sweep_2", "mom_sweep_3",
+              "psi_sweep_1", "psi_sweep_2", "psi_sweep_3")
+
+
+def step_bytes(cells, nm, ne, w, d=3):
+    """Algorithmic bytes of one whole step: the sum over its kernels."""
+    return sum(kernel_bytes(k, cells, nm, ne, w, d) for k in STEP_SLOTS)
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_3976_gb300", "csrc")
@@ -340,6 +349,7 @@ def run_ours(args, rank, world, local):
     hbm, peak_kind = peaks()
     ab = kernel_bytes(dom, cells, nm, ne, w)
     achieved = ab / (per_launch[dom] * 1e-3) / 1e9
+    sb = step_bytes(cells, nm, ne, w)
     diag = g.diagnostics()
     tuned = g.sweep_configs()
     g.close()
@@ -359,6 +369,9 @@ def run_ours(args, rank, world, local):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom)},
+        "step_roofline": {"algorithmic_bytes": sb, "GB_per_s": sb / (ms_step * 1e-3) / 1e9,
+                          "frac": sb / (ms_step * 1e-3) / 1e9 / hbm,
+                          "what": "sum of the kernels' algorithmic bytes per step / ms_per_step"},
         "gpu_launches": args.steps * (11 if nm else 7),
         "clocks": clk,
         "state_check": {"volume": diag["volume"], "div_l2": diag["div_l2"], "kinetic": diag["kinetic"]},
@@ -380,16 +393,45 @@ def run_ours(args, rank, world, local):
             out["fp64"] = {"value": cells * world / (ms64 * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms64,
                            "steps_per_s": 1e3 / ms64 * world, "steps": k64,
                            "kernels_ms_per_launch": {k: round(v, 5) for k, v in p64.items()}}
+        from paper_1305_3976_gb300 import inputs as I
         # line-solve microbench: the paper's Poisson-comparison problem
         out["line_solve_table"] = line_solve_leg(ib, torch, dev, flush, hbm)
         head = [r for r in out["line_solve_table"] if r["n"] == 512 and r["dtype"] == "f32" and r["r"] == "psi"][0]
         out["line_solve"] = {"workload": "(1-D_xx)(1-D_yy)(1-D_zz) psi = f, 512^3 FP32, r = N^2, 3 sweeps",
                              "ms": head["ms"], "GB_per_s": head["GB_per_s"], "frac": head["frac"],
                              "cell_updates_per_s": head["cell_updates_per_s"]}
+        # the 512^3 precision-scaling scene: 8 randomly oriented ellipsoids of
+        # 64002 markers each, mu = 0.01, dt = 3.125e-5; FP32 and FP64 fields
+        sc3 = I.random_ellipsoids_3d()
+        cells3, nm3, ne3 = sc3.cells, sc3.X.shape[0], sc3.edges.shape[0]
+        big = {}
+        for prec3, k3 in (("fp32", 10), ("fp64", 3)):
+            g3 = ib.Grid(3, sc3.n, rho=sc3.rho, mu=sc3.mu, dt=sc3.dt, chi=sc3.chi, precision=prec3,
+                         kernel=sc3.kernel, rotate_split=True)
+            g3.add_fiber(sc3.X, sc3.edges, sc3.kappa, sc3.rest, sc3.tris)
+            ms3 = max_over_ranks(timed_steps(g3, k3, 3)) / k3
+            flush.zero_()
+            torch.cuda.synchronize()
+            p3 = g3.profile(1)
+            g3.close()
+            w3 = 4 if prec3 == "fp32" else 8
+            sb3 = step_bytes(cells3, nm3, ne3, w3)
+            dom3 = max(p3, key=p3.get)
+            ab3 = kernel_bytes(dom3, cells3, nm3, ne3, w3)
+            big[prec3] = {"ms_per_step": ms3, "value": cells3 * world / (ms3 * 1e-3), "unit": "cell-updates/s",
+                          "steps": k3, "step_GB_per_s": sb3 / (ms3 * 1e-3) / 1e9,
+                          "step_frac": sb3 / (ms3 * 1e-3) / 1e9 / hbm,
+                          "dominant_kernel": {"kernel": dom3, "ms": p3[dom3],
+                                              "GB_per_s": ab3 / (p3[dom3] * 1e-3) / 1e9,
+                                              "frac": ab3 / (p3[dom3] * 1e-3) / 1e9 / hbm},
+                          "kernels_ms_per_launch": {k: round(v, 5) for k, v in p3.items()}}
+        out["step_512"] = {"workload": "8 randomly oriented ellipsoidal membranes (semi-axes U[0.05,0.1], "
+                                       "icosahedral nu=80, 64002 markers each), 512^3, mu=0.01, dt=3.125e-5",
+                           "cells": cells3, "markers": nm3, "springs": ne3,
+                           "l2": "inputs larger than L2; also flushed before every timed step", **big}
         # batched ensemble: 48 independent runs (N in {48, 64, 96, 128}, sigma
         # log-uniform in [0.1, 10], mu uniform in [0.01, 0.1]), one graph
         # launch per ensemble step, against the same members stepped one by one
-        from paper_1305_3976_gb300 import inputs as I
         members = I.ensemble_members(count=48)
         grids = []
         for sc_m in members:
