@@ -209,16 +209,18 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
 }
 
 // The same right-hand side for n_x divisible by 4: a thread computes one
-// component at 4 consecutive x cells from 128-bit row loads, on a
-// (x/4, y, z * d + c) launch grid.  The arithmetic per cell is the one above.
+// component at 4 consecutive x cells from 128-bit row loads.  A CTA holds d
+// warps, one per component, on the same 128 cells of an x line, so the rows
+// the components share (the other components' velocities, p, psi) are fetched
+// into the SM's L1 once for all of them; launch grid (n_x / 128, n_y, n_z).
+// The arithmetic per cell is the one above.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_rhs4(const RhsArgs<T> a) {
+__global__ void __launch_bounds__(32 * DIM) k_rhs4(const RhsArgs<T> a) {
   pdl_wait();
   pdl_release();
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z / DIM, c = blockIdx.z - (blockIdx.z / DIM) * DIM;
-  if (x0 >= a.n[0] || y >= a.n[1]) return;
+  const int y = blockIdx.y, z = blockIdx.z, c = threadIdx.y;
+  if (x0 >= a.n[0]) return;
   if (c == 0) rhs4_component<T, DIM, 0>(a, x0, y, z);
   else if (c == 1) rhs4_component<T, DIM, 1>(a, x0, y, z);
   else if (DIM == 3) rhs4_component<T, DIM, DIM == 3 ? 2 : 1>(a, x0, y, z);
@@ -346,9 +348,8 @@ template <typename T>
 cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {  // FP64 keeps the scalar kernel (register pressure)
     if ((a.n[0] & 3) == 0) {
-      const dim3 blk(32, 8);
-      const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)((a.n[1] + 7) / 8),
-                      (unsigned)((dim == 3 ? a.n[2] : 1) * dim));
+      const dim3 blk(32, dim);
+      const dim3 grid((unsigned)((a.n[0] / 4 + 31) / 32), (unsigned)a.n[1], (unsigned)(dim == 3 ? a.n[2] : 1));
       if (dim == 2) return launch_pdl(k_rhs4<T, 2>, grid, blk, 0, s, a);
       return launch_pdl(k_rhs4<T, 3>, grid, blk, 0, s, a);
     }
