@@ -332,6 +332,18 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
       }
     }
   }
+  // EARLY: the epilogue's old values (u^n or p) are loaded with the
+  // right-hand sides, so their latency hides behind the solve
+  constexpr bool EARLY = PRO == PRO_LOAD && EPI != EPI_STORE;
+  T old4[EARLY ? R : 1][4];
+  if (EARLY && vec) {
+    const T *tgt = EPI == EPI_ADDU ? a.uo[comp] : a.p;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i0 = (r * 32 + lane) * 4;
+      if (i0 < nx) ld4(tgt + base + i0, old4[EARLY ? r : 0]);
+    }
+  }
   if (PRO == PRO_DIV) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -370,7 +382,12 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
     } else if (EPI == EPI_ADDU && vec) {
       if (i0 < nx) {
         T uu[4];
-        ld4(a.uo[comp] + base + i0, uu);
+        if (EARLY) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) uu[e] = old4[EARLY ? r : 0][e];
+        } else {
+          ld4(a.uo[comp] + base + i0, uu);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) uu[e] = fma(v[r][e], sc, uu[e]);
         st4(a.uo[comp] + base + i0, uu);
@@ -378,7 +395,12 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
     } else if (EPI == EPI_P && vec) {
       if (i0 < nx) {
         T pp[4];
-        ld4(a.p + base + i0, pp);
+        if (EARLY) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) pp[e] = old4[EARLY ? r : 0][e];
+        } else {
+          ld4(a.p + base + i0, pp);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) pp[e] += v[r][e];
         st4(F + base + i0, v[r]);
@@ -458,6 +480,10 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
   const int o0 = base + start * stride;
   T v[CH][VW];
   T pn[PRO == PRO_DIV ? CH : 1][VW];
+  // EARLY: the epilogue's old values (u^n or p) are loaded with the
+  // right-hand sides, so their latency hides behind the solve
+  constexpr bool EARLY = PRO == PRO_LOAD && EPI != EPI_STORE;
+  T old[EARLY ? CH : 1][VW];
   if (PRO == PRO_LOAD) {
 #pragma unroll
     for (int e = 0; e < CH; ++e) {
@@ -466,6 +492,12 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
 #pragma unroll
         for (int c = 0; c < VW; ++c) v[e][c] = T(0);
       }
+    }
+    if (EARLY) {
+      const T *tgt = EPI == EPI_ADDU ? a.uo[comp] : a.p;
+#pragma unroll
+      for (int e = 0; e < CH; ++e)
+        if (xok && (FULL || e < len)) ldv<VW>(tgt + o0 + e * stride, old[EARLY ? e : 0]);
     }
   } else {
     // Step 3e right-hand side -rho/dt D.u^{n+1}; the new D.u and p are stored
@@ -610,10 +642,15 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
 #pragma unroll
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) {
-        T old[VW];
-        ldv<VW>(tgt + o0 + e * stride, old);
+        T ol[VW];
+        if (EARLY) {
 #pragma unroll
-        for (int c = 0; c < VW; ++c) v[e][c] = EPI == EPI_ADDU ? fma(v[e][c], sc, old[c]) : v[e][c] + old[c];
+          for (int c = 0; c < VW; ++c) ol[c] = old[EARLY ? e : 0][c];
+        } else {
+          ldv<VW>(tgt + o0 + e * stride, ol);
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[e][c] = EPI == EPI_ADDU ? fma(v[e][c], sc, ol[c]) : v[e][c] + ol[c];
       }
 #pragma unroll
     for (int e = 0; e < CH; ++e)
