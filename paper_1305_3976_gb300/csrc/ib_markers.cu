@@ -204,10 +204,22 @@ struct StencilNodes3 {
   }
 };
 
-// 4 consecutive values r[xs .. xs+3] of a row, periodic in x; aligned
-// 128-bit loads (the second only when xs is not 4-aligned) when the 8-float
-// block around xs lies inside the row
+// 4 consecutive values r[xs .. xs+3] of a row, periodic in x: one aligned
+// 256-bit load when the window lies in one 8-float block (5 of 8 offsets,
+// n_x divisible by 8), else aligned 128-bit loads (the second only when xs is
+// not 4-aligned) when the 8-float block around xs lies inside the row
 __device__ __forceinline__ void row4(const float *r, int xs, int nx, float (&v)[4]) {
+  const int a8 = xs & ~7, off8 = xs - a8;
+  if ((nx & 7) == 0 && off8 <= 4) {
+    float t[8];
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(t[0]), "=f"(t[1]), "=f"(t[2]), "=f"(t[3]), "=f"(t[4]), "=f"(t[5]), "=f"(t[6]), "=f"(t[7])
+                 : "l"(r + a8));
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      v[i] = off8 == 0 ? t[i] : off8 == 1 ? t[i + 1] : off8 == 2 ? t[i + 2] : off8 == 3 ? t[i + 3] : t[i + 4];
+    return;
+  }
   const int a0 = xs & ~3;
   if ((nx & 3) == 0 && a0 + 8 <= nx) {
     const int off = xs - a0;
