@@ -1,10 +1,13 @@
-"""Interpolation and spreading paths against the oracle (FP64 fields).
+"""Interpolation and spreading against the oracle.
 
-The marker kernels work on patches of consecutive markers whose stencils fit
-a shared-memory box, and take a direct path when they do not.  These cases
-exercise both paths and the periodic wrap of unwrapped positions:
+Interpolation gathers each stencil row with one 256-bit load when the 4-node
+window lies in one 8-float block, else with 128-bit loads, else (rows that
+wrap around the periodic box in x) with single loads; 3D spreading issues one
+atomic per node from a warp per (marker, component), 2D spreading 128-bit
+vector atomics per row.  These cases exercise every window offset and the
+periodic wrap of unwrapped positions:
   - markers scattered uniformly through the box, joined by long connections
-    (most patches exceed the box budget: direct path);
+    (every offset within a row, rows that wrap in x, y and z), FP64 and FP32;
   - a membrane translated by one period in x (unwrapped node indices in
     [n, 2n): wrapped on loads and stores, the results match the untranslated
     oracle run to rounding);
@@ -48,6 +51,18 @@ def test_scattered_markers_direct_path(dim):
     assert e["X"] < 1e-13, e
 
 
+def test_scattered_markers_fp32_3d():
+    # FP32 fields take the 256-bit / 128-bit / single-load row gathers
+    n = 32
+    X = I.random_markers(3, 700, seed=12)
+    edges = np.stack([np.arange(699), np.arange(1, 700)], axis=1).astype(np.int32)
+    sc = I.Scene(dim=3, n=(n,) * 3, rho=1.0, mu=0.05, dt=2e-4, steps=3, X=X, edges=edges,
+                 kappa=np.full(699, 0.5), rest=np.zeros(699))
+    e = run_pair(sc, 3, "fp32")
+    assert e["u"] < 1e-5, e
+    assert e["X"] < 1e-6 / n, e
+
+
 def test_membrane_one_period_away():
     sc = small_ellipsoid(n=32, nu=8)
     sc.X = sc.X + np.array([1.0, 0.0, -1.0])
@@ -64,7 +79,7 @@ def test_fiber_across_the_periodic_boundary_2d():
     assert e["X"] < 1e-13, e
 
 
-def test_fp32_patches_match_fp64_patches_at_full_size():
+def test_fp32_matches_fp64_at_full_size():
     sc = I.ellipsoid_3d(n=128, nu=64)
     out = {}
     for prec in ("fp32", "fp64"):
