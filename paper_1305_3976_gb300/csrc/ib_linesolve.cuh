@@ -460,7 +460,12 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
   pdl_wait();
   pdl_release();
   __shared__ T sz[W][VW][33];
+  __shared__ T stot[VW][32];
   __shared__ T lp[CH + 1];  // lam^0 .. lam^CH
+  // SCAN1 (FP64): warp 0 alone turns the chunk ends into the chunk prefixes
+  // (W operations per column instead of W per column and warp), the same
+  // operation sequence as every warp's own scan; FP32 keeps the per-warp scan
+  constexpr bool SCAN1 = sizeof(T) == 8;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nx = a.n[0], ny = a.n[1];
   const int x0 = (blockIdx.x * 32 + lane) * VW;
@@ -570,12 +575,34 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
   }
   __syncthreads();
   const T pstart = ld_ro(pw + min(start, nl));
+  if (SCAN1) {
+    if (w == 0) {
+#pragma unroll
+      for (int c = 0; c < VW; ++c) {
+        T run = T(0);
+        for (int q = 0; q < W; ++q) {
+          const T zq = sz[q][c][lane];
+          sz[q][c][lane] = run;
+          run = fma(run, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), zq);
+        }
+        stot[c][lane] = run;
+      }
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int c = 0; c < VW; ++c) {
-    T cin = T(0);
-    for (int q = 0; q < w; ++q) cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
-    T tot = cin;
-    for (int q = w; q < W; ++q) tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+    T cin = T(0), tot;
+    if (SCAN1) {
+      cin = sz[w][c][lane];
+      tot = stot[c][lane];
+    } else {
+      for (int q = 0; q < w; ++q)
+        cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+      tot = cin;
+      for (int q = w; q < W; ++q)
+        tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+    }
     const T t = fma(pstart, tot * a.co.inv_1m, cin);
 #pragma unroll
     for (int e = 0; e < CH; ++e)
@@ -597,16 +624,36 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
     for (int c = 0; c < VW; ++c) sz[w][c][lane] = z[c];
   }
   __syncthreads();
+  if (SCAN1) {
+    if (w == 0) {
+#pragma unroll
+      for (int c = 0; c < VW; ++c) {
+        T run = T(0);
+        for (int q = W - 1; q >= 0; --q) {
+          const T zq = sz[q][c][lane];
+          sz[q][c][lane] = run;
+          run = fma(run, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), zq);
+        }
+        stot[c][lane] = run;
+      }
+    }
+    __syncthreads();
+  }
   if (FULL || len > 0) {
     const T pend = ld_ro(pw + (nl - start - len));
 #pragma unroll
     for (int c = 0; c < VW; ++c) {
-      T cin = T(0);
-      for (int q = W - 1; q > w; --q)
-        cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
-      T tot = cin;
-      for (int q = w; q >= 0; --q)
-        tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+      T cin = T(0), tot;
+      if (SCAN1) {
+        cin = sz[w][c][lane];
+        tot = stot[c][lane];
+      } else {
+        for (int q = W - 1; q > w; --q)
+          cin = fma(cin, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+        tot = cin;
+        for (int q = w; q >= 0; --q)
+          tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
+      }
       const T t = fma(pend, tot * a.co.inv_1m, cin);
 #pragma unroll
       for (int e = 0; e < CH; ++e)
