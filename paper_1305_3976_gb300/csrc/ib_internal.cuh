@@ -95,7 +95,12 @@ struct RhsArgs {
   T *Nold[3];     // in: N(u^{n-1}); out: N(u^n)
   T *scr[3];      // out: R = u* - u^n without the force term (spreading adds dt/rho f)
   T inv_h[3], inv_h2[3];
-  T mu, inv_rho, dt;
+  // R = cmu L u + ncg_c (p* - p*(-c)) + ncA N^n + cN N^{n-1} with the
+  // Laplacian L u = sum_a (u(+a) + u(-a)) / h_a^2 - 2 u sum_a 1 / h_a^2
+  // (its coefficients cancel exactly on a constant field)
+  T cmu;          // dt mu / rho
+  T ncg[3];       // -dt / (rho h_a)
+  T ncA, cN;      // -3/2 dt and 1/2 dt (n == 0: -dt and 0)
   int n[3];
   int first;      // n == 0: p* = 0 and N^{1/2} = N(u^0)
 };

@@ -87,9 +87,11 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
         }
         adv = fma(q4[ax], sp * up[c][ax] - sm * um[c][ax], adv);
       }
-      const T gp = (p0 - pm[c]) * a.inv_h[c];
-      const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[c];
-      R[c] = a.dt * ((a.mu * lap - gp) * a.inv_rho - Nh);
+      // dt mu/rho L u - dt/rho G p* - dt (3/2 N^n - 1/2 N^{n-1}) (n == 0: - dt N^0)
+      T acc = a.cmu * lap;
+      acc = fma(a.ncg[c], p0 - pm[c], acc);
+      acc = fma(a.ncA, adv, acc);
+      R[c] = fma(a.cN, nold[c], acc);
       Nn[c] = adv;
     }
 #pragma unroll
@@ -199,9 +201,10 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
       }
       adv = fma(q4[ax], sp * up - sm * um, adv);
     }
-    const T gp = (P0[e] - Pm[e]) * a.inv_h[C];
-    const T Nh = a.first ? adv : T(1.5) * adv - T(0.5) * nold[e];
-    Rv[e] = a.dt * ((a.mu * lap - gp) * a.inv_rho - Nh);
+    T acc = a.cmu * lap;
+    acc = fma(a.ncg[C], P0[e] - Pm[e], acc);
+    acc = fma(a.ncA, adv, acc);
+    Rv[e] = fma(a.cN, nold[e], acc);
     Nn[e] = adv;
   }
   st4(a.scr[C] + ro + x0, Rv);

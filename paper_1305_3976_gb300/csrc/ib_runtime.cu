@@ -268,12 +268,16 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
     ra.inv_h2[a] = (T)(1.0 / (g->h[a] * g->h[a]));
     ra.n[a] = g->n[a];
   }
+  {
+    const double dt = g->desc.dt, rho = g->desc.rho;
+    ra.cmu = (T)(dt * g->desc.mu / rho);
+    for (int a = 0; a < 3; ++a) ra.ncg[a] = (T)(-dt / (rho * g->h[a]));
+    ra.ncA = (T)(first ? -dt : -1.5 * dt);
+    ra.cN = (T)(first ? 0.0 : 0.5 * dt);
+  }
   const bool gm1 = g->desc.scheme == IB_GM1;
   ra.p = (const T *)g->p;
   ra.psi = gm1 ? nullptr : (const T *)g->psi;
-  ra.mu = (T)g->desc.mu;
-  ra.inv_rho = (T)(1.0 / g->desc.rho);
-  ra.dt = (T)g->desc.dt;
   ra.first = first ? 1 : 0;
   IB_CUDA(launch_rhs<T>(d, ra, g->s));
   if ((rc = mark(4))) return rc;
