@@ -25,8 +25,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IB steps/s & cell-updates/s FP32 vs FP64 on one GB300; line-solve HBM GB/s"
-WORKLOAD = ("3D ellipsoidal membrane, 128^3 periodic MAC grid, rho=1, mu=0.05, semi-axes 0.2/0.25/0.3, "
-            "icosahedral nu=64 mesh (40962 markers, 122880 springs, sigma=1), dt=5e-4, FP32 fields, FP64 markers")
+
+
+def workload(n=128, nu=64, fields="FP32 fields"):
+    """The benchmark workload by name (defaults: the 128^3 configuration)."""
+    nm, ne = 10 * nu * nu + 2, 30 * nu * nu
+    return (f"3D ellipsoidal membrane, {n}^3 periodic MAC grid, rho=1, mu=0.05, semi-axes 0.2/0.25/0.3, "
+            f"icosahedral nu={nu} mesh ({nm} markers, {ne} springs, sigma=1), dt=5e-4, {fields}, FP64 markers")
+
+
+WORKLOAD = workload()
 
 
 def parse():
@@ -173,9 +181,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, tag):
     """dram bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources."""
+    was taken on the current kernel sources and on workload `tag`."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -183,7 +191,7 @@ def measured_traffic(kernel):
         t = json.load(open(p))
     except Exception:
         return None
-    if t.get("source_hash") != source_hash():
+    if t.get("source_hash") != source_hash() or t.get("workload") != tag:
         return None
     return t.get("kernels", {}).get(kernel)
 
@@ -264,7 +272,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "cell-updates/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("FP32 fields", "FP64 fields (oracle)"), "l2": "n/a (CPU)"},
+        "config": {"workload": workload(args.n, args.nu, "FP64 fields (oracle)"), "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -358,7 +366,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32 fields", "FP64 fields"),
+        "config": {"workload": workload(args.n, args.nu, "FP32 fields" if prec == "fp32" else "FP64 fields"),
                    "cells": cells, "markers": nm, "springs": ne,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "steps_per_s": 1e3 / ms_step * world,
@@ -368,7 +376,7 @@ def run_ours(args, rank, world, local):
                              for ax, t in zip(("y", "z"), tuned[1:])}},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom)},
+                     "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom, f"ellipsoid{args.n}_{prec}" if args.nu == 64 else None)},
         "step_roofline": {"algorithmic_bytes": sb, "GB_per_s": sb / (ms_step * 1e-3) / 1e9,
                           "frac": sb / (ms_step * 1e-3) / 1e9 / hbm,
                           "what": "sum of the kernels' algorithmic bytes per step / ms_per_step"},
