@@ -1,0 +1,41 @@
+"""The benchmark's algorithmic byte model and workload naming (host logic,
+no GPU).  The field kernels of one 3D step move 49 words per cell: the
+right-hand side 3d + 5 (u, p, psi, N(u^{n-1}) in; R, N(u^n) out), the
+momentum sweeps 2d, 2d and 3d (the last adds u^n), the psi sweeps d + 5 (the
+divergence prologue reads u, D.u^n and p and writes D.u^{n+1}, p and psi),
+2 and 4 (the p epilogue)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+FIELD_SLOTS = ("rhs", "mom_sweep_1", "mom_sweep_2", "mom_sweep_3", "psi_sweep_1", "psi_sweep_2", "psi_sweep_3")
+MARKER_SLOTS = ("interp", "update", "force", "spread")
+
+
+def test_field_words_per_cell():
+    for w in (4, 8):
+        cells = 128 ** 3
+        words = sum(bench.kernel_bytes(k, cells, 0, 0, w) for k in FIELD_SLOTS) / (cells * w)
+        assert words == 49
+
+
+def test_step_bytes_is_the_sum_over_the_slots():
+    cells, nm, ne = 128 ** 3, 40962, 122880
+    assert set(bench.STEP_SLOTS) == set(FIELD_SLOTS) | set(MARKER_SLOTS)
+    total = bench.step_bytes(cells, nm, ne, 4)
+    assert total == sum(bench.kernel_bytes(k, cells, nm, ne, 4) for k in bench.STEP_SLOTS)
+    # marker kernels scale with the markers and connections only
+    assert bench.step_bytes(cells, 0, 0, 4) == 49 * cells * 4
+    # the 128^3 FP32 workload: 548 345 888 bytes per step
+    assert total == 548345888
+
+
+def test_workload_names_its_grid_and_mesh():
+    assert bench.WORKLOAD == bench.workload(128, 64)
+    assert "128^3" in bench.WORKLOAD and "40962 markers" in bench.WORKLOAD and "122880 springs" in bench.WORKLOAD
+    w = bench.workload(256, 32, "FP64 fields")
+    assert "256^3" in w and "nu=32" in w and "10242 markers" in w and "FP64 fields" in w
