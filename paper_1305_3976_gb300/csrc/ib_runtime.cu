@@ -190,6 +190,8 @@ struct ib_grid_s {
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t s2 = nullptr;    // marker branch of a step (interp, update, force beside the rhs)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
 };
 
@@ -250,13 +252,25 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   T *sc[3] = {(T *)g->scr[0], (T *)g->scr[1], (T *)g->scr[2]};
   // Steps 1a-2a; spreading (Step 2b) follows the right-hand side, into which
   // it adds dt/rho f
+  // the marker chain (interp, update, force) runs on a second, higher-priority
+  // stream beside the right-hand side (they share no data); spreading waits
+  // for both.  Profiling (ev set) keeps one stream so that every kernel is
+  // timed alone.
+  const bool fork = !ev && g->nm > 0;
   if ((rc = mark(0))) return rc;
-  IB_CUDA(launch_interp<T>(m, uc, g->s));
+  cudaStream_t ms = g->s;
+  if (fork) {
+    IB_CUDA(cudaEventRecord(g->ev_fork, g->s));
+    IB_CUDA(cudaStreamWaitEvent(g->s2, g->ev_fork, 0));
+    ms = g->s2;
+  }
+  IB_CUDA(launch_interp<T>(m, uc, ms));
   if ((rc = mark(1))) return rc;
-  IB_CUDA(launch_update<T>(m, g->s));
+  IB_CUDA(launch_update<T>(m, ms));
   if ((rc = mark(2))) return rc;
-  IB_CUDA(launch_force<T>(m, g->s));
+  IB_CUDA(launch_force<T>(m, ms));
   if ((rc = mark(3))) return rc;
+  if (fork) IB_CUDA(cudaEventRecord(g->ev_join, g->s2));
   // Steps 3a-3b
   RhsArgs<T> ra;
   memset(&ra, 0, sizeof(ra));
@@ -281,6 +295,7 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   ra.first = first ? 1 : 0;
   IB_CUDA(launch_rhs<T>(d, ra, g->s));
   if ((rc = mark(4))) return rc;
+  if (fork) IB_CUDA(cudaStreamWaitEvent(g->s, g->ev_join, 0));
   // Step 2b: R += dt/rho S(X^{n+1/2}) G
   IB_CUDA(launch_spread<T>(m, sc, g->s));
   if ((rc = mark(5))) return rc;
@@ -904,9 +919,14 @@ int ib_create_grid(const ib_grid_desc *desc, ib_grid_t *out) {
     ib_destroy_grid(g);
     return rc;
   };
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithFlags(&g->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&g->s2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(fail(IB_ERR_CUDA, "stream/event creation failed"));
   const int d = g->dim;
   const int nf = 3 * d + 3;
@@ -951,6 +971,9 @@ int ib_destroy_grid(ib_grid_t g) {
   if (g->mk) cudaFree(g->mk);
   if (g->ev_in) cudaEventDestroy(g->ev_in);
   if (g->ev_out) cudaEventDestroy(g->ev_out);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->s2) cudaStreamDestroy(g->s2);
   if (g->s) cudaStreamDestroy(g->s);
   delete g;
   return IB_OK;
