@@ -360,10 +360,11 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
 
 // Step 2b: f_c(node) += G_c prod_a phi_a / h^d at X^{n+1/2}, added as
 // dt/rho f_c into the momentum increment R that the right-hand-side kernel
-// stored (Step 3b), with global atomics, one lane group per (marker, c),
-// 128-bit vector atomics per row
-// where the row segment allows.  Markers are numbered in Morton order of
-// their initial positions, so neighbouring groups update neighbouring nodes.
+// stored (Step 3b), with global atomics.  This form (used in 2D) gives each
+// (marker, c) a lane group, one row per lane, 128-bit vector atomics per row
+// where the row segment allows; 3D uses k_spread3 below.  Markers are
+// numbered in Morton order of their initial positions, so neighbouring groups
+// update neighbouring nodes.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
   pdl_wait();
