@@ -173,11 +173,16 @@ def step_bytes(cells, nm, ne, w, d=3):
 
 
 def source_hash():
+    """Hash of the CUDA sources without their // comments and blank lines, so
+    that a counter file stays valid across comment edits but not code edits."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_3976_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            for line in open(os.path.join(csrc, f), encoding="utf-8"):
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
