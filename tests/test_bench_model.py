@@ -39,3 +39,18 @@ def test_workload_names_its_grid_and_mesh():
     assert "128^3" in bench.WORKLOAD and "40962 markers" in bench.WORKLOAD and "122880 springs" in bench.WORKLOAD
     w = bench.workload(256, 32, "FP64 fields")
     assert "256^3" in w and "nu=32" in w and "10242 markers" in w and "FP64 fields" in w
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    # the oracle on a small grid: one JSON line with the reference-arm keys
+    args = type("A", (), {"steps": 2, "warmup": 1, "n": 16, "nu": 4, "gpus": 1})()
+    assert bench.run_reference(args, 0, 1) == 0
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "cell-updates/s" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["dtype"] == "f64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "16^3" in line["config"]["workload"]
