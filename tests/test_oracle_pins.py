@@ -491,8 +491,9 @@ def test_energy_decays_and_its_window_increases_vanish_with_dt():
         h = 1.0 / N
 
         def energy():
-            d = sim.X[sc.edges[:, 1]] - sim.X[sc.edges[:, 0]]
-            return 0.5 * h * h * np.sum(sim.u ** 2) + 0.5 * np.sum(sc.kappa * np.sum(d * d, axis=1))
+            # kinetic energy plus the oracle's connection energy (pinned in
+            # test_oracle_diagnostics.py: its gradient is minus the force)
+            return 0.5 * h * h * np.sum(sim.u ** 2) + O.elastic_energy(sim.X, sc.edges, sc.kappa, sc.rest)
 
         E = [energy()]
         for _ in range(int(round(T / dt)) // 10):
