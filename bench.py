@@ -141,16 +141,22 @@ class Clocks:
 
 
 def kernel_bytes(name, cells, nm, ne, w, d=3):
+    """HBM bytes of one launch: the arrays a kernel must stream from or to
+    DRAM.  The 4^d grid nodes that interpolation gathers and spreading updates
+    per marker and component are not counted: neighbouring markers share most
+    of them and they are served by L1/L2 (ncu: interpolation and spreading move
+    8.3 and 8.4 MB of DRAM per 128^3 step, their marker arrays being 7.9 MB);
+    spreading is reported in atomic updates per second instead
+    (stencil_updates)."""
     m = {
-        # locations of X^n (d slots per component: index + 4 weights), one
-        # field word per node of the 4^d stencil, U^n out
-        "interp": nm * d * (d * (4 + 4 * w) + 4 ** d * w + w),
+        # locations of X^n (d slots per component: index + 4 weights), U^n out
+        "interp": nm * d * (d * (4 + 4 * w) + w),
         # X, U, U^{n-1} in; X^{n+1}, X^{n+1/2}, U^{n-1}, both location sets out
         "update": nm * (d * 8 + 2 * d * w + 2 * d * 8 + d * w + 2 * 2 * d * (4 + 4 * w)),
         # own and neighbour X^{n+1/2}, CSR row/col/kappa/rest, G out
         "force": nm * (d * 8 + 16 + d * w) + 2 * ne * (d * 8 + 4 + 16),
-        # locations of X^{n+1/2}, G, one read-modify-write word per stencil node
-        "spread": nm * d * (d * (4 + 4 * w) + w + 4 ** d * 2 * w),
+        # locations of X^{n+1/2}, G in
+        "spread": nm * d * (d * (4 + 4 * w) + w),
         # u(3), p, psi, N(u^{n-1})(3) in; R(3), N(u^n)(3) out
         "rhs": cells * w * (3 * d + 5),
         "mom_sweep_1": cells * w * 2 * d,
@@ -161,6 +167,30 @@ def kernel_bytes(name, cells, nm, ne, w, d=3):
         "psi_sweep_3": cells * w * 4,       # psi, p in; psi, p out
     }
     return m[name]
+
+
+def stencil_updates(nm, d=3):
+    """Grid-node updates of one spreading launch (and node reads of one
+    interpolation launch): 4^d nodes per marker and component."""
+    return nm * d * 4 ** d
+
+
+def survey_step_bytes(cells, w, d=3):
+    """The per-pass byte model of a 3D step with one field round trip per
+    sweep: right-hand side 17w + force clear 3w, six x/y momentum sweeps 12w,
+    three z sweeps with u^n 9w, divergence 4w, psi x/y sweeps 4w, psi z sweep
+    with the pressure update 6w: 55 words per cell."""
+    assert d == 3
+    return 55 * w * cells
+
+
+def fp64_ops(name, cells):
+    """FP64 instructions of one launch of the FP64 right-hand side or of one
+    FP64 line-solve sweep, counted from the arithmetic: per cell and velocity
+    component 30 (Laplacian 2 + 2 per axis, skew advection 5 per axis, p* 2,
+    the R and N assembly 5); per line element 4 (the local recurrence and the
+    correction of each of the two factors)."""
+    return {"rhs": 90 * cells, "sweep": 4 * cells}[name]
 
 
 STEP_SLOTS = ("interp", "update", "force", "rhs", "spread", "mom_sweep_1", "mom_sweep_2", "mom_sweep_3",
@@ -201,6 +231,24 @@ def measured_traffic(kernel, tag):
     return t.get("kernels", {}).get(kernel)
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -209,7 +257,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def line_solve_leg(ib, torch, dev, flush, hbm, sizes=(128, 256, 512), precisions=("f32", "f64")):
+def line_solve_leg(ib, torch, dev, flush, hbm, sizes=(128, 256, 512), precisions=("f32", "f64"), fp64_ops_peak=None):
     """Sec. 6.1's Poisson-comparison problem: (1 - D_xx)(1 - D_yy)(1 - D_zz) psi
     = f with f = sin 2 pi x cos 2 pi y cos 2 pi z at the cell centres of the
     unit cube, three line-solve sweeps through ib_split_solve.  r = 1/h^2 (the
@@ -246,8 +294,12 @@ def line_solve_leg(ib, torch, dev, flush, hbm, sizes=(128, 256, 512), precisions
                 ms = tot / reps
                 nbytes = 3 * 2 * f.element_size() * N ** 3
                 gbs = nbytes / (ms * 1e-3) / 1e9
-                rows.append({"n": N, "dtype": prec, "r": kind, "ms": round(ms, 5), "GB_per_s": round(gbs, 1),
-                             "frac": round(gbs / hbm, 4), "cell_updates_per_s": N ** 3 / (ms * 1e-3)})
+                row = {"n": N, "dtype": prec, "r": kind, "ms": round(ms, 5), "GB_per_s": round(gbs, 1),
+                       "frac": round(gbs / hbm, 4), "cell_updates_per_s": N ** 3 / (ms * 1e-3)}
+                if prec == "f64" and fp64_ops_peak:
+                    ops = 3 * fp64_ops("sweep", N ** 3)
+                    row["alu_frac"] = round(ops / (ms * 1e-3) / fp64_ops_peak, 4)
+                rows.append(row)
             del f, psi
     return rows
 
@@ -278,7 +330,8 @@ def run_reference(args, rank, world):
         "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(args.n, args.nu, "FP64 fields (oracle)"), "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
         "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -339,6 +392,10 @@ def run_ours(args, rank, world, local):
 
     prec = args.precision
     w = 4 if prec == "fp32" else 8
+    # ceilings of the kernels not bound by HBM, measured on this GPU
+    unit_peaks = {"fp64_flops": ib.ib_measure_peak(ib.IB_PEAK_FP64_FMA),
+                  "fp32_flops": ib.ib_measure_peak(ib.IB_PEAK_FP32_FMA),
+                  "l2_atomics_per_s": ib.ib_measure_peak(ib.IB_PEAK_L2_ATOMIC)}
     g = make_grid(prec)
     clocks = Clocks(local)
     clocks.start()
@@ -384,7 +441,18 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": ab, "traffic": measured_traffic(dom, f"ellipsoid{args.n}_{prec}" if args.nu == 64 else None)},
         "step_roofline": {"algorithmic_bytes": sb, "GB_per_s": sb / (ms_step * 1e-3) / 1e9,
                           "frac": sb / (ms_step * 1e-3) / 1e9 / hbm,
-                          "what": "sum of the kernels' algorithmic bytes per step / ms_per_step"},
+                          "what": "sum of the kernels' HBM byte models per step / ms_per_step",
+                          "survey_model": {"bytes": survey_step_bytes(cells, w),
+                                           "GB_per_s": survey_step_bytes(cells, w) / (ms_step * 1e-3) / 1e9,
+                                           "frac": survey_step_bytes(cells, w) / (ms_step * 1e-3) / 1e9 / hbm,
+                                           "what": "55 words per cell (one field round trip per sweep)"}},
+        "spreading": {"bound": "l2_atomic", "updates_per_launch": stencil_updates(nm),
+                      "ms": per_launch["spread"],
+                      "updates_per_s": stencil_updates(nm) / (per_launch["spread"] * 1e-3),
+                      "peak": unit_peaks["l2_atomics_per_s"],
+                      "frac": stencil_updates(nm) / (per_launch["spread"] * 1e-3) / unit_peaks["l2_atomics_per_s"],
+                      "unit": "atomic updates/s"},
+        "measured_unit_peaks": unit_peaks,
         "gpu_launches": args.steps * (11 if nm else 7),
         "clocks": clk,
         "state_check": {"volume": diag["volume"], "div_l2": diag["div_l2"], "kinetic": diag["kinetic"]},
@@ -403,12 +471,23 @@ def run_ours(args, rank, world, local):
                 for k, v in g64.profile(1).items():
                     p64[k] = p64.get(k, 0.0) + v / 3
             g64.close()
+            fp64_ops_peak = unit_peaks["fp64_flops"] / 2.0     # FP64 instructions/s (one FMA = 2 FLOP)
+            alu = {}
+            for slot, kind in (("rhs", "rhs"), ("mom_sweep_1", "sweep"), ("psi_sweep_2", "sweep")):
+                ops = fp64_ops(kind, cells) * (3 if slot.startswith("mom") else 1)
+                alu[slot] = {"fp64_ops": ops, "ms": p64[slot], "achieved": ops / (p64[slot] * 1e-3),
+                             "peak": fp64_ops_peak, "frac": ops / (p64[slot] * 1e-3) / fp64_ops_peak,
+                             "unit": "FP64 instructions/s"}
             out["fp64"] = {"value": cells * world / (ms64 * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms64,
                            "steps_per_s": 1e3 / ms64 * world, "steps": k64,
+                           "alu_roofline": {"bound": "alu", "kernels": alu,
+                                            "what": "FP64 instructions counted from the arithmetic / ms, against "
+                                                    "the measured FP64 FMA issue rate (ib_measure_peak)"},
                            "kernels_ms_per_launch": {k: round(v, 5) for k, v in p64.items()}}
         from paper_1305_3976_gb300 import inputs as I
         # line-solve microbench: the paper's Poisson-comparison problem
-        out["line_solve_table"] = line_solve_leg(ib, torch, dev, flush, hbm)
+        out["line_solve_table"] = line_solve_leg(ib, torch, dev, flush, hbm,
+                                                 fp64_ops_peak=unit_peaks["fp64_flops"] / 2.0)
         head = [r for r in out["line_solve_table"] if r["n"] == 512 and r["dtype"] == "f32" and r["r"] == "psi"][0]
         out["line_solve"] = {"workload": "(1-D_xx)(1-D_yy)(1-D_zz) psi = f, 512^3 FP32, r = N^2, 3 sweeps",
                              "ms": head["ms"], "GB_per_s": head["GB_per_s"], "frac": head["frac"],
@@ -453,7 +532,7 @@ def run_ours(args, rank, world, local):
             grids.append(gm)
         ens = ib.Ensemble(grids)
         ens.step(args.warmup)
-        ke = 20
+        ke = 100
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -479,6 +558,7 @@ def run_ours(args, rank, world, local):
                            "markers": int(sum(sc_m.X.shape[0] for sc_m in members)), "steps": ke,
                            "ms_per_step": ms_e, "value": cells_e * world / (ms_e * 1e-3),
                            "unit": "cell-updates/s",
+                           "survey_model_frac": survey_step_bytes(cells_e, 4) / (ms_e * 1e-3) / 1e9 / hbm,
                            "one_by_one_ms_per_step": ms_s,
                            "one_by_one_value": cells_e * world / (ms_s * 1e-3)}
         # stiffness gradient by the discrete adjoint: 96^3 FP32 fields, 7842
@@ -509,6 +589,44 @@ def run_ours(args, rank, world, local):
                                       "200 steps, checkpoints every 20 steps",
                           **{k: {kk: (round(vv, 6) if kk != "loss" else vv) for kk, vv in v.items()}
                              for k, v in adj.items()}}
+        # the paper's timed 3D problem (Sec. 6, Table 9): the cylindrical shell
+        # (N_s = 19N/4 x N_r = 3N markers, dt = 0.04/N, mu = 0.01) at N = 128
+        # and 256 for 100 steps, FP32 and FP64 fields, L2 flushed before every
+        # step; the paper's wall times are quoted as context only
+        cyl = {}
+        for N in (128, 256):
+            scN = I.cylinder_3d(n=N)
+            row = {"markers": int(scN.X.shape[0]), "connections": int(scN.edges.shape[0])}
+            for precN in ("fp32", "fp64"):
+                gN = ib.Grid(3, scN.n, rho=scN.rho, mu=scN.mu, dt=scN.dt, chi=scN.chi, precision=precN,
+                             kernel=scN.kernel, rotate_split=True)
+                gN.add_fiber(scN.X, scN.edges, scN.kappa, scN.rest)
+                msN = max_over_ranks(timed_steps(gN, 100, 3))
+                gN.close()
+                row[precN] = {"s_per_100_steps": msN * 1e-3, "ms_per_step": msN / 100,
+                              "steps_per_s": 100 / (msN * 1e-3), "cell_updates_per_s": N ** 3 * 100 / (msN * 1e-3)}
+            cyl[str(N)] = row
+        out["cylinder"] = {"workload": "cylindrical elastic shell of Sec. 6 (axial rest length 1, closed through the "
+                                       "periodic box), N^3 grid, 100 steps, dt = 0.04/N",
+                           "rows": cyl,
+                           "paper_table9_context": {"hardware": "Intel Xeon X5650 cluster (WestGrid Bugaboo), "
+                                                                "precision unstated",
+                                                    "128": {"1_core_s": 401.0, "128_cores_s": 7.76},
+                                                    "256": {"1_core_s": 2600.0, "128_cores_s": 30.2}}}
+        # the 2D ellipse workload: 64^2, 256 markers, FP64 fields, both kernels,
+        # 100 steps (latency-bound: throughput only)
+        c1 = {}
+        for kern in ("cos4", "peskin4"):
+            sc1 = I.thin_ellipse_2d(n=64, ns=256, kernel=kern)
+            g1 = ib.Grid(2, sc1.n, rho=sc1.rho, mu=sc1.mu, dt=sc1.dt, chi=sc1.chi, precision="fp64", kernel=kern,
+                         rotate_split=True)
+            g1.add_fiber(sc1.X, sc1.edges, sc1.kappa, sc1.rest)
+            ms1 = max_over_ranks(timed_steps(g1, 100, 3))
+            g1.close()
+            c1[kern] = {"ms_per_step": ms1 / 100, "steps_per_s": 100 / (ms1 * 1e-3),
+                        "cell_updates_per_s": 64 * 64 * 100 / (ms1 * 1e-3)}
+        out["ellipse_2d"] = {"workload": "2D elliptical membrane, 64^2, 256 markers, rho=1, mu=0.1, sigma=1, "
+                                         "dt=1e-3, FP64 fields, 100 steps", **c1}
         # end to end through the C ABI with host buffers: every step the marker
         # positions come from pinned host memory and go back to it
         ge = make_grid(prec)
@@ -527,16 +645,23 @@ def run_ours(args, rank, world, local):
         out["e2e"] = {"value": cells * args.steps * world / te, "unit": "cell-updates/s",
                       "h2d_bytes_per_step": nm * 3 * 8, "d2h_bytes_per_step": nm * 3 * 8,
                       "what": "per step: ib_set_markers from pinned host memory, ib_step, ib_read_markers to host"}
-        # the oracle on this host's cores, one step of the same workload
+        # the oracle on this host's cores: one warm-up step (the n = 0 branch),
+        # then the median of 3 single steps of the same workload
         if rank == 0 and world == 1:
             import oracle as O
             P = O.params(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
             sim = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest)
-            t0 = time.perf_counter()
             sim.step(1)
-            tc = time.perf_counter() - t0
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                sim.step(1)
+                ts.append(time.perf_counter() - t0)
+            tc = float(np.median(ts))
             out["cpu_baseline"] = {"value": cells / tc, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                                   "sample": f"1 step of the {args.n}^3 workload ({tc:.1f} s, FP64, one thread)"}
+                                   "cpu": cpu_model(),
+                                   "sample": f"median of 3 single steps of the {args.n}^3 workload after one "
+                                             f"warm-up step ({tc:.2f} s per step, FP64, one thread)"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

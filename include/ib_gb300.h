@@ -113,8 +113,10 @@ int ib_create_grid(const ib_grid_desc *desc, ib_grid_t *out);
  * of N_s points with kappa = sigma / h_s and rest_len = L h_s reproduces the
  * paper's F_k h_s.  rest_len may be NULL (all zero).  tris (optional, 3D:
  * [n_tris][3] outward-oriented triangles; 2D: ignored, the directed edges give
- * the area) feed ib_diagnostics.  All arrays are host memory.  Only allowed
- * before the first step.  fiber_id_out (optional) receives the structure's
+ * the area) feed ib_diagnostics.  Every array may be host memory or device
+ * memory of the current device (told apart by cudaPointerGetAttributes; device
+ * arrays are copied to the host on the grid's stream, which the call then
+ * synchronises).  Only allowed before the first step.  fiber_id_out (optional) receives the structure's
  * index.  Errors: IB_ERR_ARG, IB_ERR_STATE, IB_ERR_OOM, IB_ERR_CUDA. */
 int ib_add_fiber(ib_grid_t g, const double *X0, int64_t n_markers, const int32_t *edges,
                  const double *kappa, const double *rest_len, int64_t n_edges,
@@ -160,10 +162,14 @@ const char *ib_error_string(int code);
 const char *ib_last_error(void);
 
 /* Ensembles of independent grids (each with its own size, parameters and
- * structures) advanced together: every step of the ensemble is one CUDA graph
- * launch in which each member's kernels form an independent branch, so the
- * members' kernels run concurrently on the GPU.  The paper runs one problem at
- * a time; this batches many.
+ * structures) advanced together.  Members of the same precision and size form
+ * a size class; every kernel of a step (Sec. 3.4, Steps 1a-3f) is one batched
+ * launch per class that walks the class's member table (at most 24 members a
+ * launch), the classes run side by side, and a whole ensemble step is one
+ * CUDA graph launch.  The paper runs one problem at a time; this batches
+ * many.  Within a class the line solves use the register kernels with the
+ * shape the class's first member chose (ib_sweep_config), so an ensemble
+ * member agrees with the same grid stepped alone to rounding.
  *   ib_create_ensemble: members are existing grids (the ensemble does not own
  *     them) that all have the same dim, the same rotate_split and the same
  *     step count; their structures must already be added.  stream: as in
@@ -210,8 +216,10 @@ int ib_split_solve(int precision, int dim, const int n[3], const double r[3], co
  *   - Line lengths are limited to IB_NOALLOC_MAX_N (= 512); a larger n[a]
  *     returns IB_ERR_ARG with a message naming the limit.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, and again after the
+ *     device's context was created anew (e.g. after cudaDeviceReset); make
+ *     that first call before any stream capture.  Devices 0 .. 63 are
+ *     supported; a call on a device with a higher index returns IB_ERR_ARG.
  *   - Every call rewrites the shared array before its solves read it, so no
  *     state carries over between calls, but calls whose work overlaps on the
  *     GPU (different streams, or different host threads) race on the array:
@@ -301,6 +309,21 @@ int ib_load_state(ib_grid_t g, const void *src, size_t bytes);
  * Synchronises `stream` (a cudaStream_t; NULL: default stream).
  * Errors: IB_ERR_ARG, IB_ERR_CUDA. */
 int ib_selftest_wait_timeout(void *stream, int *timed_out);
+
+/* Throughput probes of the current GPU (no counterpart in the paper), the
+ * ceilings of the step's kernels that are not bound by HBM bandwidth:
+ *   IB_PEAK_FP64_FMA   FP64 fused multiply-adds, in FLOP/s (2 per FMA): the
+ *                      FP64 right-hand side and line solves;
+ *   IB_PEAK_FP32_FMA   the same in FP32;
+ *   IB_PEAK_L2_ATOMIC  float atomic adds without return, each warp instruction
+ *                      on 32 consecutive floats of an L2-resident 16 MB
+ *                      buffer, in updates/s: spreading (Step 2b).
+ * Runs 3 warm-up and 5 timed launches on `stream` (a cudaStream_t; NULL:
+ * default stream), timed by CUDA events, and writes the best rate to *value
+ * (host).  Allocates and frees a 16 MB scratch buffer; synchronises the
+ * stream.  Errors: IB_ERR_ARG (kind, null value), IB_ERR_OOM, IB_ERR_CUDA. */
+enum { IB_PEAK_FP64_FMA = 0, IB_PEAK_FP32_FMA = 1, IB_PEAK_L2_ATOMIC = 2 };
+int ib_measure_peak(int kind, void *stream, double *value);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,8 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
            "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
            "ib_sweep_config", "ib_fix_sweep_config", "ib_adjoint_run", "ib_selftest_wait_timeout",
-           "ib_state_size", "ib_save_state", "ib_load_state")
+           "ib_state_size", "ib_save_state", "ib_load_state", "ib_measure_peak")
+IB_PEAK_FP64_FMA, IB_PEAK_FP32_FMA, IB_PEAK_L2_ATOMIC = 0, 1, 2
 
 
 class ib_grid_desc(C.Structure):
@@ -78,6 +79,7 @@ def lib():
         L.ib_create_ensemble.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
         L.ib_ensemble_step.argtypes = [vp, C.c_int]
         L.ib_destroy_ensemble.argtypes = [vp]
+        L.ib_measure_peak.argtypes = [C.c_int, vp, dp]
         L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.ib_fix_sweep_config.argtypes = [vp, C.c_int, C.c_int]
         L.ib_adjoint_run.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp]
@@ -153,17 +155,30 @@ def ib_create_grid(dim, n, H=1.0, rho=1.0, mu=0.1, dt=1e-3, chi=0.6, precision=I
 
 
 def ib_add_fiber(g, X0, edges, kappa, rest_len=None, tris=None):
-    X0 = np.ascontiguousarray(X0, dtype=np.float64)
-    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
-    k = np.ascontiguousarray(kappa, dtype=np.float64)
-    r = None if rest_len is None else np.ascontiguousarray(rest_len, dtype=np.float64)
-    t = None if tris is None else np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
-    fid = C.c_int32()
+    """Arrays may be numpy (host) or contiguous torch CUDA tensors (device) of
+    the C types: X0 float64 [n][dim], edges int32 [n_edges][2], kappa and
+    rest_len float64 [n_edges], tris int32 [n_tris][3]."""
     dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
-    _check(lib().ib_add_fiber(g, X0.ctypes.data_as(dp), X0.shape[0], e.ctypes.data_as(ip), k.ctypes.data_as(dp),
-                              None if r is None else r.ctypes.data_as(dp), e.shape[0],
-                              None if t is None else t.ctypes.data_as(ip), 0 if t is None else t.shape[0],
-                              C.byref(fid)), "ib_add_fiber")
+
+    def arr(x, dtype, cols, ctype):
+        if x is None:
+            return None, 0
+        if _is_torch_cuda(x):
+            if not x.is_contiguous() or x.element_size() != np.dtype(dtype).itemsize:
+                raise ValueError("device arrays must be contiguous tensors of the C type")
+            return C.cast(C.c_void_p(x.data_ptr()), ctype), x.numel() // cols
+        a = np.ascontiguousarray(x, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data_as(ctype), a.size // cols
+
+    keep = []
+    X0p, nm = arr(X0, np.float64, X0.shape[-1] if hasattr(X0, "shape") else 1, dp)
+    ep, ne = arr(edges, np.int32, 2, ip)
+    kp, _ = arr(kappa, np.float64, 1, dp)
+    rp, _ = arr(rest_len, np.float64, 1, dp)
+    tp, nt = arr(tris, np.int32, 3, ip)
+    fid = C.c_int32()
+    _check(lib().ib_add_fiber(g, X0p, nm, ep, kp, rp, ne, tp, nt, C.byref(fid)), "ib_add_fiber")
     return fid.value
 
 
@@ -201,6 +216,15 @@ def ib_diagnostics(g, check=True):
     if check:
         _check(rc, "ib_diagnostics")
     return {k: getattr(d, k) for k, _ in ib_diag._fields_}, rc
+
+
+def ib_measure_peak(kind, stream="current"):
+    """Throughput of one of the GPU's units (IB_PEAK_*): FLOP/s or atomic
+    updates/s."""
+    v = C.c_double()
+    st = _current_stream() if stream == "current" else stream
+    _check(lib().ib_measure_peak(int(kind), st, C.byref(v)), "ib_measure_peak")
+    return v.value
 
 
 def ib_destroy_grid(g):
@@ -322,8 +346,8 @@ class Grid:
 
     def add_fiber(self, X, edges, kappa, rest=None, tris=None):
         fid = ib_add_fiber(self.h, X, edges, kappa, rest, tris)
-        self.n_markers += np.asarray(X).shape[0]
-        self.n_edges += np.asarray(edges).reshape(-1, 2).shape[0]
+        self.n_markers += len(X)
+        self.n_edges += (edges if hasattr(edges, "reshape") else np.asarray(edges)).reshape(-1, 2).shape[0]
         return fid
 
     def set_velocity(self, u):

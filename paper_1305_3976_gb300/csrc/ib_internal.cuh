@@ -32,6 +32,80 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Block coordinates of a kernel body.  An ordinary launch passes the hardware
+// blockIdx / gridDim (hw_blk); a batched launch -- the grids of one ensemble
+// size class stepped by a single launch -- passes each member's own block
+// index and grid inside its share of the launch (batch_member).
+struct Blk {
+  unsigned x, y, z;     // block index
+  unsigned gx, gy, gz;  // grid size
+};
+__device__ __forceinline__ Blk hw_blk() { return Blk{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z}; }
+
+// Arguments of a batched launch, passed by value as one kernel parameter
+// (constant bank): per member its arguments and its own 3-D grid; the
+// launch's 1-D grid is the concatenation of the members' grids.
+constexpr int kBatch = 24;
+template <typename A>
+struct Batch {
+  A a[kBatch];
+  unsigned start[kBatch + 1];  // first block of member m; start[n] = blocks of the launch
+  unsigned gx[kBatch], gy[kBatch];
+  int n;
+};
+
+// the member that owns this block and the block's coordinates in its grid
+template <typename A>
+__device__ __forceinline__ int batch_member(const Batch<A> &B, Blk &b) {
+  const unsigned v = blockIdx.x;
+  int m = 0;
+  while (m + 1 < B.n && v >= B.start[m + 1]) ++m;
+  const unsigned l = v - B.start[m], gx = B.gx[m], gy = B.gy[m];
+  b.x = l % gx;
+  b.y = (l / gx) % gy;
+  b.z = l / (gx * gy);
+  b.gx = gx;
+  b.gy = gy;
+  b.gz = (B.start[m + 1] - B.start[m]) / (gx * gy);
+  return m;
+}
+
+// Launch `kernel` over n members (args[i] with grid grids[i]), kBatch members
+// per launch, with smem bytes of dynamic shared memory per CTA; `extra`
+// follows the batch in the kernel's parameters.
+template <typename A, typename K, typename... Extra>
+cudaError_t launch_batch_smem(K kernel, const A *args, const dim3 *grids, int n, dim3 block, size_t smem,
+                              cudaStream_t s, Extra... extra) {
+  for (int c0 = 0; c0 < n; c0 += kBatch) {
+    Batch<A> B;
+    const int k = n - c0 < kBatch ? n - c0 : kBatch;
+    unsigned tot = 0;
+    for (int i = 0; i < kBatch; ++i) {
+      if (i < k) {
+        B.a[i] = args[c0 + i];
+        B.gx[i] = grids[c0 + i].x;
+        B.gy[i] = grids[c0 + i].y;
+      } else {
+        B.a[i] = args[c0];
+        B.gx[i] = B.gy[i] = 1;
+      }
+      B.start[i] = tot;
+      if (i < k) tot += grids[c0 + i].x * grids[c0 + i].y * grids[c0 + i].z;
+    }
+    B.start[kBatch] = tot;
+    B.n = k;
+    if (tot == 0) continue;
+    cudaError_t e = launch_pdl(kernel, dim3(tot), block, smem, s, B, extra...);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+template <typename A, typename K, typename... Extra>
+cudaError_t launch_batch(K kernel, const A *args, const dim3 *grids, int n, dim3 block, cudaStream_t s,
+                         Extra... extra) {
+  return launch_batch_smem(kernel, args, grids, n, block, 0, s, extra...);
+}
+
 // 4 contiguous elements at p (16-byte aligned for float, 32 for double)
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4 *>(p);
@@ -60,13 +134,57 @@ __device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
 // 1 / (1 - lam^n).  The scale is applied once, in the sweep's epilogue: a
 // chain of sweeps (each one linear) passes 1 in all sweeps but the last,
 // which carries the product of the chain's 1/c.
+//
+// The periodic correction of each factor -- the rank-one term
+// lam^{i+1} z_{n-1} / (1 - lam^n) (Sherman-Morrison on the factor), combined
+// with a chunk's carry-in c as t = lam^{i0} K + c, K = z_{n-1} / (1 - lam^n)
+// -- is evaluated to FP64 accuracy when wrap_ext is set (FP32 fields whose
+// wrap weight lam^n is above FP32 resolution, e.g. the psi operator with
+// r = 1/h^2, where lam^n is about e^-1): the FP64 host values of lam^{i0} and
+// 1/(1 - lam^n) are split into FP32 pairs hi + lo, and the product and sum
+// are carried in two-float arithmetic (wrap_term_ext), so t is rounded to FP32
+// once.  FP64 instructions would do the same at 1/64 of the FP32 rate on this
+// GPU's FP64 pipe.
 template <typename T>
 struct LineCoef {
-  const T *pw;  // lam^k for k = 0 .. n  (device)
+  const T *pw;     // lam^k for k = 0 .. n  (device)
   T lam;
-  T scale;      // factor applied to the solution: 1 / c for one complete solve
-  T inv_1m;     // 1 / (1 - lam^n)
+  T scale;         // factor applied to the solution: 1 / c for one complete solve
+  T inv_1m;        // 1 / (1 - lam^n)
+  const T *pw_lo;  // FP32: lam^k - pw[k] in FP32 (device; read when wrap_ext)
+  T inv_1m_lo;     // FP32: 1 / (1 - lam^n) - inv_1m
+  int wrap_ext;    // FP64-accurate periodic correction (T = float only)
 };
+
+// t = (p_hi + p_lo) tot (q_hi + q_lo) + cin in two-float arithmetic: the
+// rounding error of each product comes exactly from an FMA and that of the
+// final sum from Knuth's two-sum, so about 46 significant bits reach the one
+// rounding to FP32.  The expressions are evaluated in source order (no
+// reassociation without fast-math flags).
+__device__ __forceinline__ float wrap_term_ext(float p_hi, float p_lo, float q_hi, float q_lo, float tot, float cin) {
+  const float k_hi = tot * q_hi;
+  const float k_lo = fmaf(tot, q_lo, fmaf(tot, q_hi, -k_hi));
+  const float m_hi = p_hi * k_hi;
+  const float m_lo = fmaf(p_hi, k_lo, fmaf(p_lo, k_hi, fmaf(p_hi, k_hi, -m_hi)));
+  const float s = m_hi + cin;
+  const float bb = s - m_hi;
+  const float e = (m_hi - (s - bb)) + (cin - bb);
+  return s + (e + m_lo);
+}
+__device__ __forceinline__ double wrap_term_ext(double, double, double, double, double tot, double cin) {
+  return tot + cin;  // not used: FP64 fields take the plain correction
+}
+
+// t = lam^{i0} tot / (1 - lam^n) + cin for a chunk starting at element i0 of
+// a line whose non-periodic end value (the factor's carry over all chunks) is
+// tot
+// tot (EXT: to FP64 accuracy; the kernels are instantiated with EXT for the
+// FP32 solves whose LineCoef::wrap_ext is set)
+template <bool EXT, typename T>
+__device__ __forceinline__ T wrap_term(const LineCoef<T> &co, int i0, T tot, T cin) {
+  if (EXT) return wrap_term_ext(__ldg(co.pw + i0), __ldg(co.pw_lo + i0), co.inv_1m, co.inv_1m_lo, tot, cin);
+  return fma(__ldg(co.pw + i0), tot * co.inv_1m, cin);
+}
 
 enum { PRO_LOAD = 0, PRO_DIV = 1 };
 enum { EPI_STORE = 0, EPI_ADDU = 1, EPI_P = 2 };
@@ -131,6 +249,13 @@ struct MarkerArgs {
   int n[3];
   int dim, kernel, first;
   int frac_force;       // force from the stored locations of X^{n+1/2} (FP32 fields)
+};
+
+// marker arguments with three field pointers: the velocity interpolation
+// reads (const) or the momentum increments spreading adds to
+struct MarkerFieldArgs {
+  MarkerArgs m;
+  void *f[3];
 };
 
 // strided line solves staged by TMA (see ib_sweep_tma.cu): FP32, y and z
@@ -224,6 +349,27 @@ cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s);
 
 cudaError_t launch_markers_layout(double *aos, double *const X[3], const int32_t *perm, int64_t nm, int dim,
                                   int to_soa, cudaStream_t s);
+
+// batched launches over n grids of one ensemble size class (same dim and
+// precision; see launch_batch)
+template <typename T>
+cudaError_t launch_interp_batch(const MarkerFieldArgs *a, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_batch(const MarkerArgs *m, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_force_batch(const MarkerArgs *m, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread_batch(const MarkerFieldArgs *a, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rhs_batch(int dim, const RhsArgs<T> *a, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sweep_batch(int axis, int pro, int epi, int nfields, const SweepArgs<T> *a, int n,
+                               cudaStream_t s, int cfg);
+// the FP32 sweeps with the FP64-accurate periodic correction (LineCoef::wrap_ext)
+cudaError_t launch_sweep_f32_ext(int axis, int pro, int epi, int nfields, const SweepArgs<float> &a, cudaStream_t s,
+                                 int cfg);
+cudaError_t launch_sweep_batch_f32_ext(int axis, int pro, int epi, int nfields, const SweepArgs<float> *a, int n,
+                                       cudaStream_t s, int cfg);
 
 struct DiagAccum {
   double div2, divmax, kin, vol, elastic, nonfinite;

@@ -2,6 +2,8 @@
 // the FP64 diagnostics, for sm_103a.
 #include <math.h>
 
+#include <vector>
+
 #include "ib_internal.cuh"
 
 namespace ibg {
@@ -17,13 +19,11 @@ namespace ibg {
 // transport velocity A+- (the a-velocity averaged to the two flux points half
 // a cell above and below the c-face) add up to 1/2 (A+ u_c(+a) - A- u_c(-a))/h_a.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
-  pdl_wait();
-  pdl_release();
+__device__ __forceinline__ void rhs_body(const RhsArgs<T> &a, const Blk &B) {
   const int nx = a.n[0], ny = a.n[1], nz = DIM == 3 ? a.n[2] : 1;
   const long long cells = (long long)nx * ny * nz;
   // cell counts stay below 2^31 (n <= 512 per axis): 32-bit index arithmetic
-  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < (unsigned)cells; o += gridDim.x * blockDim.x) {
+  for (unsigned o = B.x * blockDim.x + threadIdx.x; o < (unsigned)cells; o += B.gx * blockDim.x) {
     const int i = (int)(o % (unsigned)nx);
     const unsigned tq = o / (unsigned)nx;
     const int j = (int)(tq % (unsigned)ny);
@@ -100,6 +100,20 @@ __global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
       a.Nold[c][o] = Nn[c];
     }
   }
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_rhs(const RhsArgs<T> a) {
+  pdl_wait();
+  pdl_release();
+  rhs_body<T, DIM>(a, hw_blk());
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_rhs_b(const __grid_constant__ Batch<RhsArgs<T>> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  rhs_body<T, DIM>(Bt.a[i], b);
 }
 
 // 4 values of a row at x0 + shift .. x0 + 3 + shift (shift in {-1, 0, 1}),
@@ -218,15 +232,27 @@ __device__ __forceinline__ void rhs4_component(const RhsArgs<T> &a, int x0, int 
 // into the SM's L1 once for all of them; launch grid (n_x / 128, n_y, n_z).
 // The arithmetic per cell is the one above.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(32 * DIM) k_rhs4(const RhsArgs<T> a) {
-  pdl_wait();
-  pdl_release();
-  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y, z = blockIdx.z, c = threadIdx.y;
+__device__ __forceinline__ void rhs4_body(const RhsArgs<T> &a, const Blk &B) {
+  const int x0 = 4 * (B.x * blockDim.x + threadIdx.x);
+  const int y = B.y, z = B.z, c = threadIdx.y;
   if (x0 >= a.n[0]) return;
   if (c == 0) rhs4_component<T, DIM, 0>(a, x0, y, z);
   else if (c == 1) rhs4_component<T, DIM, 1>(a, x0, y, z);
   else if (DIM == 3) rhs4_component<T, DIM, DIM == 3 ? 2 : 1>(a, x0, y, z);
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(32 * DIM) k_rhs4(const RhsArgs<T> a) {
+  pdl_wait();
+  pdl_release();
+  rhs4_body<T, DIM>(a, hw_blk());
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(32 * DIM) k_rhs4_b(const __grid_constant__ Batch<RhsArgs<T>> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  rhs4_body<T, DIM>(Bt.a[i], b);
 }
 
 template <typename T, int DIM>
@@ -362,6 +388,27 @@ cudaError_t launch_rhs(int dim, const RhsArgs<T> &a, cudaStream_t s) {
   if (dim == 2) return launch_pdl(k_rhs<T, 2>, dim3(g), dim3(256), 0, s, a);
   return launch_pdl(k_rhs<T, 3>, dim3(g), dim3(256), 0, s, a);
 }
+
+// all members share dim, precision and n (one ensemble size class)
+template <typename T>
+cudaError_t launch_rhs_batch(int dim, const RhsArgs<T> *a, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  std::vector<dim3> g(n);
+  if constexpr (sizeof(T) == 4) {
+    if ((a[0].n[0] & 3) == 0) {
+      for (int i = 0; i < n; ++i)
+        g[i] = dim3((unsigned)((a[i].n[0] / 4 + 31) / 32), (unsigned)a[i].n[1], (unsigned)(dim == 3 ? a[i].n[2] : 1));
+      if (dim == 2) return launch_batch(k_rhs4_b<T, 2>, a, g.data(), n, dim3(32, 2), s);
+      return launch_batch(k_rhs4_b<T, 3>, a, g.data(), n, dim3(32, 3), s);
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    g[i] = dim3(grid_stride_blocks((long long)a[i].n[0] * a[i].n[1] * (dim == 3 ? a[i].n[2] : 1)));
+  if (dim == 2) return launch_batch(k_rhs_b<T, 2>, a, g.data(), n, dim3(256), s);
+  return launch_batch(k_rhs_b<T, 3>, a, g.data(), n, dim3(256), s);
+}
+template cudaError_t launch_rhs_batch<float>(int, const RhsArgs<float> *, int, cudaStream_t);
+template cudaError_t launch_rhs_batch<double>(int, const RhsArgs<double> *, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_divergence(int dim, const T *const u[3], T *div, const int n[3], const T inv_h[3],

@@ -25,6 +25,8 @@
 // Each element is read once and written once: 2 words of HBM traffic.
 #pragma once
 
+#include <vector>
+
 #include "ib_internal.cuh"
 
 namespace ibg {
@@ -33,6 +35,16 @@ namespace ibg {
 
 template <typename T>
 __device__ __forceinline__ T ld_ro(const T *p) { return __ldg(p); }
+// 4 contiguous elements through the read-only path (alignment as ld4)
+__device__ __forceinline__ void ld4_ro(const float *p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4_ro(const double *p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 
 __device__ __forceinline__ int next_wrap(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 
@@ -91,6 +103,28 @@ __device__ __forceinline__ void ldv(const T *p, T (&v)[VW]) {
     v[0] = *p;
   }
 }
+// the same through the read-only path
+template <int VW, typename T>
+__device__ __forceinline__ void ldv_ro(const T *p, T (&v)[VW]) {
+  if (VW == 4) {
+    T t[4];
+    ld4_ro(p, t);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) v[i] = t[i];
+  } else if (VW == 2) {
+    if (sizeof(T) == 4) {
+      const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+      v[0] = (T)t.x;
+      v[VW - 1] = (T)t.y;
+    } else {
+      const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+      v[0] = (T)t.x;
+      v[VW - 1] = (T)t.y;
+    }
+  } else {
+    v[0] = __ldg(p);
+  }
+}
 template <int VW, typename T>
 __device__ __forceinline__ void stv(T *p, const T (&v)[VW]) {
   if (VW == 4) {
@@ -112,10 +146,17 @@ struct XLineCoef {
   T gk[5];      // lam^(4 * 2^k)
   T gf, gb;     // gains of lanes 0..lane and lane..31
   T pf[R], pb[R];  // lam^(i0) and lam^(n - i0 - 4) of this lane's chunks
-  __device__ __forceinline__ void load(const LineCoef<T> &co, int n, int lane) {
+  T inv_1m_lo;     // FP64-accurate periodic correction (EXT): the FP32 remainders
+  const T *pw_lo;
+  int n;
+  __device__ __forceinline__ void load(const LineCoef<T> &co, int n_, int lane) {
+    const int n = n_;
+    this->n = n_;
     const T *pw = co.pw;
     lam = co.lam;
     inv_1m = co.inv_1m;
+    inv_1m_lo = co.inv_1m_lo;
+    pw_lo = co.pw_lo;
     l2 = ld_ro(pw + 2);
     l3 = ld_ro(pw + 3);
     l4 = ld_ro(pw + 4);
@@ -132,7 +173,7 @@ struct XLineCoef {
 };
 
 // Solve one x line held by a warp: v[r][e] is element (32 r + lane) * 4 + e.
-template <typename T, int R>
+template <typename T, int R, bool EXT>
 __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, int lane, T (&v)[R][4]) {
   const T lam = co.lam;
   const T *pw = co.pw;
@@ -159,12 +200,13 @@ __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, in
     cin[r] = lane == 0 ? carry : Sx;
     carry = __shfl_sync(IBG_FULL, S, 31);
   }
-  T K = carry * co.inv_1m;  // periodic wrap: y_{-1} = z_{n-1} / (1 - lam^n)
+  // periodic wrap: y_{-1} = z_{n-1} / (1 - lam^n)
+  T tot = carry;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i0 = (r * 32 + lane) * 4;
     const int len = max(0, min(4, n - i0));
-    const T t = fma(ld_ro(pw + min(i0, n)), K, cin[r]);
+    const T t = wrap_term<EXT>(co, min(i0, n), tot, cin[r]);
 #pragma unroll
     for (int e = 0; e < 4; ++e)
       if (e < len) v[r][e] = fma(ld_ro(pw + e + 1), t, v[r][e]);
@@ -191,13 +233,13 @@ __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, in
     cin[r] = lane == 31 ? carry : Sx;
     carry = __shfl_sync(IBG_FULL, S, 0);
   }
-  K = carry * co.inv_1m;  // x_n = x_0 = w_0 / (1 - lam^n)
+  tot = carry;  // x_n = x_0 = w_0 / (1 - lam^n)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i0 = (r * 32 + lane) * 4;
     const int len = max(0, min(4, n - i0));
     if (len > 0) {
-      const T t = fma(ld_ro(pw + (n - i0 - len)), K, cin[r]);
+      const T t = wrap_term<EXT>(co, n - i0 - len, tot, cin[r]);
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         if (e < len) v[r][e] = fma(ld_ro(pw + (len - e)), t, v[r][e]);
@@ -209,7 +251,7 @@ __device__ __forceinline__ void solve_line_warp(const LineCoef<T> &co, int n, in
 // so every chunk's gain is lam^4 and a window of 2^k chunks has gain
 // lam^(4 2^k); the scan then shuffles only the partial sums and all powers
 // live in registers.
-template <typename T, int R>
+template <typename T, int R, bool EXT>
 __device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, int lane, T (&v)[R][4]) {
   const T lam = c.lam;
   T cin[R];
@@ -235,7 +277,9 @@ __device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, i
   T K = carry * c.inv_1m;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const T t = fma(c.pf[r], K, cin[r]);
+    const T t = EXT ? wrap_term_ext(c.pf[r], __ldg(c.pw_lo + (r * 32 + lane) * 4), c.inv_1m, c.inv_1m_lo, carry,
+                                      cin[r])
+                      : fma(c.pf[r], K, cin[r]);
     v[r][0] = fma(lam, t, v[r][0]);
     v[r][1] = fma(c.l2, t, v[r][1]);
     v[r][2] = fma(c.l3, t, v[r][2]);
@@ -263,7 +307,9 @@ __device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, i
   K = carry * c.inv_1m;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const T t = fma(c.pb[r], K, cin[r]);
+    const T t = EXT ? wrap_term_ext(c.pb[r], __ldg(c.pw_lo + (c.n - (r * 32 + lane) * 4 - 4)), c.inv_1m,
+                                      c.inv_1m_lo, carry, cin[r])
+                      : fma(c.pb[r], K, cin[r]);
     v[r][0] = fma(c.l4, t, v[r][0]);
     v[r][1] = fma(c.l3, t, v[r][1]);
     v[r][2] = fma(c.l2, t, v[r][2]);
@@ -272,7 +318,7 @@ __device__ __forceinline__ void solve_line_warp_full(const XLineCoef<T, R> &c, i
 }
 
 // one x line per warp and loop iteration; blockIdx.y selects the field
-template <typename T, int R, int PRO, int EPI, bool FULL>
+template <typename T, int R, int PRO, int EPI, bool FULL, bool EXT>
 __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineCoef<T, R> &xc, T *F, const T *Fin,
                                              int comp, long long line, int lane) {
   const int nx = a.n[0], ny = a.n[1];
@@ -289,14 +335,18 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
       if (i0 < nx) ld4(Fin + base + i0, v[r]);
       else { v[r][0] = v[r][1] = v[r][2] = v[r][3] = T(0); }
     } else if (PRO == PRO_DIV && vec) {
-      T u4[4], vj[4], vj1[4], d4[4], p4[4];
+      // read-only loads (every element is read before this thread alone
+      // writes it), and the new D.u and p stored at once: nothing of the
+      // prologue stays live across the rounds
+      T u4[4] = {T(0), T(0), T(0), T(0)}, vj[4] = {T(0), T(0), T(0), T(0)}, vj1[4] = {T(0), T(0), T(0), T(0)};
+      T d4[4] = {T(0), T(0), T(0), T(0)}, p4[4] = {T(0), T(0), T(0), T(0)};
       const T *u0 = a.u[0], *u1 = a.u[1];
       if (i0 < nx) {
-        ld4(u0 + base + i0, u4);
-        ld4(u1 + base + i0, vj);
-        ld4(u1 + base + (long long)nx * (next_wrap(j, ny) - j) + i0, vj1);
-        ld4(a.div + base + i0, d4);
-        ld4(a.p + base + i0, p4);
+        ld4_ro(u0 + base + i0, u4);
+        ld4_ro(u1 + base + i0, vj);
+        ld4_ro(u1 + base + (long long)nx * (next_wrap(j, ny) - j) + i0, vj1);
+        ld4_ro(a.div + base + i0, d4);
+        ld4_ro(a.p + base + i0, p4);
       }
       // u at face i0 + 4: the next lane's first element, or a load at the end
       // of a round / the periodic wrap at the end of the line
@@ -305,18 +355,23 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
       if (i0 < nx && (lane == 31 || i0 + 4 >= nx)) unext = ld_ro(u0 + base + (i0 + 4 < nx ? i0 + 4 : 0));
       T w4[4] = {T(0), T(0), T(0), T(0)}, wk1[4] = {T(0), T(0), T(0), T(0)};
       if (a.dim == 3 && i0 < nx) {
-        ld4(a.u[2] + base + i0, w4);
-        ld4(a.u[2] + base + (long long)nx * ny * (next_wrap(k, a.n[2]) - k) + i0, wk1);
+        ld4_ro(a.u[2] + base + i0, w4);
+        ld4_ro(a.u[2] + base + (long long)nx * ny * (next_wrap(k, a.n[2]) - k) + i0, wk1);
       }
+      T dn4[4], pn4[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const T up = e < 3 ? u4[e + 1] : unext;
         T d = (up - u4[e]) * a.inv_h[0];
         d += (vj1[e] - vj[e]) * a.inv_h[1];
         if (a.dim == 3) d += (wk1[e] - w4[e]) * a.inv_h[2];
-        dn[PRO == PRO_DIV ? r : 0][e] = d;
-        pn[PRO == PRO_DIV ? r : 0][e] = kept_p(a, p4[e]) - a.chi_mu_half * (d + d4[e]);
+        dn4[e] = d;
+        pn4[e] = kept_p(a, p4[e]) - a.chi_mu_half * (d + d4[e]);
         v[r][e] = i0 < nx ? a.pro_scale * d : T(0);
+      }
+      if (i0 < nx) {
+        st4(a.div + base + i0, dn4);
+        st4(a.p + base + i0, pn4);
       }
     } else {
 #pragma unroll
@@ -344,16 +399,11 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
       if (i0 < nx) ld4(tgt + base + i0, old4[EARLY ? r : 0]);
     }
   }
-  if (PRO == PRO_DIV) {
+  if (PRO == PRO_DIV && !vec) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i0 = (r * 32 + lane) * 4;
-      if (vec) {
-        if (i0 < nx) {
-          st4(a.div + base + i0, dn[PRO == PRO_DIV ? r : 0]);
-          st4(a.p + base + i0, pn[PRO == PRO_DIV ? r : 0]);
-        }
-      } else {
+      {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           if (i0 + e < nx) {
@@ -363,8 +413,8 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
       }
     }
   }
-  if (FULL) solve_line_warp_full<T, R>(xc, lane, v);
-  else solve_line_warp<T, R>(a.co, nx, lane, v);
+  if (FULL) solve_line_warp_full<T, R, EXT>(xc, lane, v);
+  else solve_line_warp<T, R, EXT>(a.co, nx, lane, v);
   // the scale 1/c (EPI_ADDU folds it into the sum); skipped in the unscaled
   // sweeps of a chain
   const T sc = a.co.scale;
@@ -430,23 +480,34 @@ __device__ __forceinline__ void sweep_x_line(const SweepArgs<T> &a, const XLineC
   }
 }
 
-template <typename T, int R, int PRO, int EPI, bool FULL>
-__global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
-  pdl_wait();
-  pdl_release();
+template <typename T, int R, int PRO, int EPI, bool FULL, bool EXT>
+__device__ __forceinline__ void sweep_x_body(const SweepArgs<T> &a, const Blk &B) {
   const int lane = threadIdx.x & 31;
   const int nx = a.n[0], ny = a.n[1];
   const long long nlines = (long long)ny * (a.dim == 3 ? a.n[2] : 1);
-  const int comp = blockIdx.y;
+  const int comp = B.y;
   T *F = a.f[comp];
   const T *Fin = a.fin[comp] ? a.fin[comp] : F;
   XLineCoef<T, R> xc;
   if (FULL) xc.load(a.co, nx, lane);
   // each warp solves lines warp, warp + W, ... (W warps in the grid)
-  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < nlines;
-       line += wstride)
-    sweep_x_line<T, R, PRO, EPI, FULL>(a, xc, F, Fin, comp, line, lane);
+  const long long wstride = (long long)B.gx * (blockDim.x >> 5);
+  for (long long line = (long long)B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); line < nlines; line += wstride)
+    sweep_x_line<T, R, PRO, EPI, FULL, EXT>(a, xc, F, Fin, comp, line, lane);
+}
+template <typename T, int R, int PRO, int EPI, bool FULL, bool EXT>
+__global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
+  pdl_wait();
+  pdl_release();
+  sweep_x_body<T, R, PRO, EPI, FULL, EXT>(a, hw_blk());
+}
+template <typename T, int R, int PRO, int EPI, bool FULL, bool EXT>
+__global__ void __launch_bounds__(256) k_sweep_x_b(const __grid_constant__ Batch<SweepArgs<T>> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  sweep_x_body<T, R, PRO, EPI, FULL, EXT>(Bt.a[i], b);
 }
 
 // strided lines along axis 1 (y) or 2 (z); a thread owns VW adjacent x
@@ -455,10 +516,8 @@ __global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
 // blockIdx.z: the field.  FULL: the line length is exactly W * CH, so no
 // element needs a bounds test.  Element offsets fit in 32 bits (at most 512^3
 // elements per field).
-template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL>
-__global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const int axis) {
-  pdl_wait();
-  pdl_release();
+template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL, bool EXT>
+__device__ __forceinline__ void sweep_s_body(const SweepArgs<T> &a, const int axis, const Blk &B) {
   __shared__ T sz[W][VW][33];
   __shared__ T stot[VW][32];
   __shared__ T lp[CH + 1];  // lam^0 .. lam^CH
@@ -468,9 +527,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
   constexpr bool SCAN1 = sizeof(T) == 8;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nx = a.n[0], ny = a.n[1];
-  const int x0 = (blockIdx.x * 32 + lane) * VW;
-  const int other = blockIdx.y;
-  const int comp = blockIdx.z;
+  const int x0 = (B.x * 32 + lane) * VW;
+  const int other = B.y;
+  const int comp = B.z;
   if (threadIdx.x <= CH) lp[threadIdx.x] = ld_ro(a.co.pw + threadIdx.x);
   T *F = a.f[comp];
   const T *Fin = a.fin[comp] ? a.fin[comp] : F;
@@ -484,7 +543,6 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
   const T *pw = a.co.pw;
   const int o0 = base + start * stride;
   T v[CH][VW];
-  T pn[PRO == PRO_DIV ? CH : 1][VW];
   // EARLY: the epilogue's old values (u^n or p) are loaded with the
   // right-hand sides, so their latency hides behind the solve
   constexpr bool EARLY = PRO == PRO_LOAD && EPI != EPI_STORE;
@@ -511,50 +569,44 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
     const int jo = axis == 1 ? -1 : other, ko = axis == 1 ? other : -1;  // fixed coordinate
     const int xe = x0 + VW == nx ? -x0 : VW;   // offset of the face after the last column
 #pragma unroll
+    // read-only loads (every element is read before this thread alone writes
+    // it) and the new D.u and p stored at once, so that only the right-hand
+    // sides stay live
     for (int e = 0; e < CH; ++e) {
 #pragma unroll
-      for (int c = 0; c < VW; ++c) v[e][c] = pn[PRO == PRO_DIV ? e : 0][c] = T(0);
+      for (int c = 0; c < VW; ++c) v[e][c] = T(0);
       if (xok && (FULL || e < len)) {
         const int t = start + e;
         const int j = axis == 1 ? t : jo, k = axis == 1 ? ko : t;
         const int o = o0 + e * stride;
         const int dy = j + 1 == ny ? nx * (1 - ny) : nx;
         T u0[VW], v0[VW], v1[VW], dv[VW], pv[VW];
-        ldv<VW>(a.u[0] + o, u0);
+        ldv_ro<VW>(a.u[0] + o, u0);
         const T ue = ld_ro(a.u[0] + o + xe);
-        ldv<VW>(a.u[1] + o, v0);
-        ldv<VW>(a.u[1] + o + dy, v1);
-        ldv<VW>(a.div + o, dv);
-        ldv<VW>(a.p + o, pv);
+        ldv_ro<VW>(a.u[1] + o, v0);
+        ldv_ro<VW>(a.u[1] + o + dy, v1);
+        ldv_ro<VW>(a.div + o, dv);
+        ldv_ro<VW>(a.p + o, pv);
         T w0[VW], w1[VW];
         if (a.dim == 3) {
           const int dz = k + 1 == nz ? nx * ny * (1 - nz) : nx * ny;
-          ldv<VW>(a.u[2] + o, w0);
-          ldv<VW>(a.u[2] + o + dz, w1);
+          ldv_ro<VW>(a.u[2] + o, w0);
+          ldv_ro<VW>(a.u[2] + o + dz, w1);
         }
+        T dn[VW], pn[VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) {
           const T up = c + 1 < VW ? u0[c + 1 < VW ? c + 1 : 0] : ue;
           T d = (up - u0[c]) * a.inv_h[0];
           d += (v1[c] - v0[c]) * a.inv_h[1];
           if (a.dim == 3) d += (w1[c] - w0[c]) * a.inv_h[2];
-          pn[PRO == PRO_DIV ? e : 0][c] = kept_p(a, pv[c]) - a.chi_mu_half * (d + dv[c]);
+          dn[c] = d;
+          pn[c] = kept_p(a, pv[c]) - a.chi_mu_half * (d + dv[c]);
           v[e][c] = a.pro_scale * d;
         }
+        stv<VW>(a.div + o, dn);
+        stv<VW>(a.p + o, pn);
       }
-    }
-    if (xok) {
-      const T inv_scale = T(1) / a.pro_scale;
-#pragma unroll
-      for (int e = 0; e < CH; ++e)
-        if (FULL || e < len) {
-          const int o = o0 + e * stride;
-          T dnew[VW];
-#pragma unroll
-          for (int c = 0; c < VW; ++c) dnew[c] = v[e][c] * inv_scale;
-          stv<VW>(a.div + o, dnew);
-          stv<VW>(a.p + o, pn[PRO == PRO_DIV ? e : 0]);
-        }
     }
   }
   __syncthreads();  // lp
@@ -603,7 +655,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
       for (int q = w; q < W; ++q)
         tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
     }
-    const T t = fma(pstart, tot * a.co.inv_1m, cin);
+    const T t = EXT ? wrap_term<true>(a.co, min(start, nl), tot, cin) : fma(pstart, tot * a.co.inv_1m, cin);
 #pragma unroll
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) v[e][c] = fma(lp[e + 1], t, v[e][c]);
@@ -654,7 +706,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
         for (int q = w; q >= 0; --q)
           tot = fma(tot, FULL ? gCH : ld_ro(pw + max(0, min(CH, nl - q * CH))), sz[q][c][lane]);
       }
-      const T t = fma(pend, tot * a.co.inv_1m, cin);
+      const T t = EXT ? wrap_term<true>(a.co, nl - start - len, tot, cin) : fma(pend, tot * a.co.inv_1m, cin);
 #pragma unroll
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) {
@@ -703,6 +755,21 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const 
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) stv<VW>(tgt + o0 + e * stride, v[e]);
   }
+}
+template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL, bool EXT>
+__global__ void __launch_bounds__(32 * W) k_sweep_s(const SweepArgs<T> a, const int axis) {
+  pdl_wait();
+  pdl_release();
+  sweep_s_body<T, VW, CH, W, PRO, EPI, FULL, EXT>(a, axis, hw_blk());
+}
+template <typename T, int VW, int CH, int W, int PRO, int EPI, bool FULL, bool EXT>
+__global__ void __launch_bounds__(32 * W) k_sweep_s_b(const __grid_constant__ Batch<SweepArgs<T>> Bt,
+                                                      const int axis) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  sweep_s_body<T, VW, CH, W, PRO, EPI, FULL, EXT>(Bt.a[i], axis, b);
 }
 
 // Sweep configurations.  Strided lines (axes 1, 2): VW adjacent x columns
@@ -754,7 +821,7 @@ inline int strided_cfg_default(int nl, int nx, bool dbl, bool div) {
 }
 
 // line lengths 8 <= n <= 512 (checked by the caller); cfg < 0: default
-template <typename T, int PRO, int EPI>
+template <typename T, int PRO, int EPI, bool EXT>
 cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStream_t s, int cfg) {
   const int nl = a.n[axis];
   if (axis == 0) {
@@ -763,12 +830,12 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
     const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
     dim3 grid((unsigned)(ctas < cap ? ctas : cap), nfields);  // warps loop over lines
     const dim3 b(256);
-    if (nl == 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, true>, grid, b, 0, s, a);
-    if (nl < 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, false>, grid, b, 0, s, a);
-    if (nl == 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, true>, grid, b, 0, s, a);
-    if (nl < 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, false>, grid, b, 0, s, a);
-    if (nl == 512) return launch_pdl(k_sweep_x<T, 4, PRO, EPI, true>, grid, b, 0, s, a);
-    return launch_pdl(k_sweep_x<T, 4, PRO, EPI, false>, grid, b, 0, s, a);
+    if (nl == 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, true, EXT>, grid, b, 0, s, a);
+    if (nl < 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, false, EXT>, grid, b, 0, s, a);
+    if (nl == 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, true, EXT>, grid, b, 0, s, a);
+    if (nl < 256) return launch_pdl(k_sweep_x<T, 2, PRO, EPI, false, EXT>, grid, b, 0, s, a);
+    if (nl == 512) return launch_pdl(k_sweep_x<T, 4, PRO, EPI, true, EXT>, grid, b, 0, s, a);
+    return launch_pdl(k_sweep_x<T, 4, PRO, EPI, false, EXT>, grid, b, 0, s, a);
   } else {
     const int other = axis == 1 ? (a.dim == 3 ? a.n[2] : 1) : a.n[1];
     const int nx = a.n[0];
@@ -780,8 +847,8 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
   case I: {                                                                                             \
     constexpr StridedCfg c = strided_cfg(I);                                                            \
     if (nl == c.ch * c.w)                                                                               \
-      return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
-    return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
+      return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
+    return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
   }
     if constexpr (sizeof(T) == 8) {
       switch (cfg) { IBG_S(0) IBG_S(3) IBG_S(6) IBG_S(8) IBG_S(10) default: return cudaErrorInvalidValue; }
@@ -801,13 +868,75 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
   return cudaGetLastError();
 }
 
-template <typename T>
+// The same sweeps for n grids of one size class in batched launches (the
+// register kernels only; every member has the same n, precision and dim)
+template <typename T, int PRO, int EPI, bool EXT>
+cudaError_t launch_sweep_batch_t(int axis, int nfields, const SweepArgs<T> *a, int n, cudaStream_t s, int cfg) {
+  const SweepArgs<T> &a0 = a[0];
+  const int nl = a0.n[axis];
+  std::vector<dim3> g(n);
+  if (axis == 0) {
+    const long long nlines = (long long)a0.n[1] * (a0.dim == 3 ? a0.n[2] : 1);
+    const long long ctas = (nlines + 7) / 8;
+    const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
+    for (int i = 0; i < n; ++i) g[i] = dim3((unsigned)(ctas < cap ? ctas : cap), nfields);
+    const dim3 b(256);
+    if (nl == 128) return launch_batch(k_sweep_x_b<T, 1, PRO, EPI, true, EXT>, a, g.data(), n, b, s);
+    if (nl < 128) return launch_batch(k_sweep_x_b<T, 1, PRO, EPI, false, EXT>, a, g.data(), n, b, s);
+    if (nl == 256) return launch_batch(k_sweep_x_b<T, 2, PRO, EPI, true, EXT>, a, g.data(), n, b, s);
+    if (nl < 256) return launch_batch(k_sweep_x_b<T, 2, PRO, EPI, false, EXT>, a, g.data(), n, b, s);
+    if (nl == 512) return launch_batch(k_sweep_x_b<T, 4, PRO, EPI, true, EXT>, a, g.data(), n, b, s);
+    return launch_batch(k_sweep_x_b<T, 4, PRO, EPI, false, EXT>, a, g.data(), n, b, s);
+  }
+  const int other = axis == 1 ? (a0.dim == 3 ? a0.n[2] : 1) : a0.n[1];
+  const int nx = a0.n[0];
+  const bool dbl = sizeof(T) == 8, div = PRO == PRO_DIV;
+  if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl, div)) cfg = strided_cfg_default(nl, nx, dbl, div);
+  auto grids = [&](int v) {
+    for (int i = 0; i < n; ++i) g[i] = dim3((unsigned)((nx / v + 31) / 32), other, nfields);
+    return g.data();
+  };
+#define IBG_SB(I)                                                                                           \
+  case I: {                                                                                                 \
+    constexpr StridedCfg c = strided_cfg(I);                                                                \
+    if (nl == c.ch * c.w)                                                                                   \
+      return launch_batch(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, a, grids(c.vw), n, dim3(32 * c.w), s, axis); \
+    return launch_batch(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, a, grids(c.vw), n, dim3(32 * c.w), s, axis); \
+  }
+  if constexpr (sizeof(T) == 8) {
+    switch (cfg) { IBG_SB(0) IBG_SB(3) IBG_SB(6) IBG_SB(8) IBG_SB(10) default: return cudaErrorInvalidValue; }
+  } else if constexpr (PRO == PRO_DIV) {
+    switch (cfg) {
+      IBG_SB(0) IBG_SB(1) IBG_SB(3) IBG_SB(4) IBG_SB(6) IBG_SB(8) IBG_SB(10)
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (cfg) {
+      IBG_SB(0) IBG_SB(1) IBG_SB(2) IBG_SB(3) IBG_SB(4) IBG_SB(5) IBG_SB(6) IBG_SB(7) IBG_SB(8) IBG_SB(9) IBG_SB(10)
+      default: return cudaErrorInvalidValue;
+    }
+  }
+#undef IBG_SB
+}
+
+template <typename T, bool EXT>
+cudaError_t launch_sweep_batch_impl(int axis, int pro, int epi, int nfields, const SweepArgs<T> *a, int n,
+                                    cudaStream_t s, int cfg) {
+  if (n < 1) return cudaSuccess;
+  if (pro == PRO_LOAD && epi == EPI_STORE) return launch_sweep_batch_t<T, PRO_LOAD, EPI_STORE, EXT>(axis, nfields, a, n, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_ADDU) return launch_sweep_batch_t<T, PRO_LOAD, EPI_ADDU, EXT>(axis, nfields, a, n, s, cfg);
+  if (pro == PRO_DIV && epi == EPI_STORE) return launch_sweep_batch_t<T, PRO_DIV, EPI_STORE, EXT>(axis, nfields, a, n, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_P) return launch_sweep_batch_t<T, PRO_LOAD, EPI_P, EXT>(axis, nfields, a, n, s, cfg);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, bool EXT>
 cudaError_t launch_sweep_impl(int axis, int pro, int epi, int nfields, const SweepArgs<T> &a, cudaStream_t s,
                               int cfg) {
-  if (pro == PRO_LOAD && epi == EPI_STORE) return launch_sweep_t<T, PRO_LOAD, EPI_STORE>(axis, nfields, a, s, cfg);
-  if (pro == PRO_LOAD && epi == EPI_ADDU) return launch_sweep_t<T, PRO_LOAD, EPI_ADDU>(axis, nfields, a, s, cfg);
-  if (pro == PRO_DIV && epi == EPI_STORE) return launch_sweep_t<T, PRO_DIV, EPI_STORE>(axis, nfields, a, s, cfg);
-  if (pro == PRO_LOAD && epi == EPI_P) return launch_sweep_t<T, PRO_LOAD, EPI_P>(axis, nfields, a, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_STORE) return launch_sweep_t<T, PRO_LOAD, EPI_STORE, EXT>(axis, nfields, a, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_ADDU) return launch_sweep_t<T, PRO_LOAD, EPI_ADDU, EXT>(axis, nfields, a, s, cfg);
+  if (pro == PRO_DIV && epi == EPI_STORE) return launch_sweep_t<T, PRO_DIV, EPI_STORE, EXT>(axis, nfields, a, s, cfg);
+  if (pro == PRO_LOAD && epi == EPI_P) return launch_sweep_t<T, PRO_LOAD, EPI_P, EXT>(axis, nfields, a, s, cfg);
   return cudaErrorInvalidValue;
 }
 

@@ -12,6 +12,8 @@
 // stencil nodes and their 4 weights.
 #include <math.h>
 
+#include <vector>
+
 #include "ib_internal.cuh"
 
 namespace ibg {
@@ -101,10 +103,8 @@ __global__ void __launch_bounds__(256) k_locate(const MarkerArgs m, double *cons
 // and the grid locations of X^{n+1/2} (spreading, this step) and of X^{n+1}
 // (interpolation, next step).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
-  pdl_wait();
-  pdl_release();
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void update_body(const MarkerArgs &m, const Blk &B) {
+  const unsigned t = B.x * blockDim.x + threadIdx.x;
   const unsigned k = t / DIM;
   const int c = (int)(t - k * DIM);
   if (k >= (unsigned)m.nm) return;
@@ -122,6 +122,20 @@ __global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
   store_location<T>(m, Xh, c, k, m.locS_b, (T *)m.locS_w, (T *)m.locS_f);
   store_location<T>(m, Xn, c, k, m.locI_b, (T *)m.locI_w);
 }
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_update(const MarkerArgs m) {
+  pdl_wait();
+  pdl_release();
+  update_body<T, DIM>(m, hw_blk());
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_update_b(const __grid_constant__ Batch<MarkerArgs> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  update_body<T, DIM>(Bt.a[i], b);
+}
 
 // Lane groups for the 4^d-node stencils: one group of ROWS lanes per
 // (marker, component c) (16 in 3D, 4 in 2D); lane r owns the stencil row
@@ -135,9 +149,9 @@ struct StencilLanes {
   bool valid;
   T wx[4], wrow;  // x weights; product of this row's y (and z) weights
   int bx, yrow, zrow;
-  __device__ __forceinline__ StencilLanes(const MarkerArgs &m, const int32_t *lb, const T *lw) {
+  __device__ __forceinline__ StencilLanes(const MarkerArgs &m, const int32_t *lb, const T *lw, const Blk &B) {
     // 32-bit index arithmetic: marker count * d * ROWS < 2^31 (checked on the host)
-    const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned gt = B.x * blockDim.x + threadIdx.x;
     const unsigned pair = gt / ROWS;
     row = (int)(gt & (ROWS - 1));
     k = pair / DIM;
@@ -178,9 +192,9 @@ struct StencilNodes3 {
   bool valid;
   T w0, w1;
   unsigned o0, o1;  // element offsets of the two nodes (fields hold < 2^31 elements)
-  __device__ __forceinline__ StencilNodes3(const MarkerArgs &m, const int32_t *lb, const T *lw) {
+  __device__ __forceinline__ StencilNodes3(const MarkerArgs &m, const int32_t *lb, const T *lw, const Blk &B) {
     // 32-bit unsigned thread index: at most 2^25 markers (checked on the host), 96 lanes each
-    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned gw = (B.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     k = gw / 3;
     c = (int)(gw - k * 3);
@@ -264,11 +278,9 @@ __device__ __forceinline__ void row4_add(double *r, int xs, int nx, const double
 
 // Step 1a: U_c = sum over the 4^d nodes of u_c(node) prod_a phi_a, at X^n.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
-                                                const T *const u2) {
-  pdl_wait();
-  pdl_release();
-  StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w);
+__device__ __forceinline__ void interp_body(const MarkerArgs &m, const T *const u0, const T *const u1,
+                                            const T *const u2, const Blk &B) {
+  StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w, B);
   T s = T(0);
   if (L.valid) {
     const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
@@ -279,6 +291,21 @@ __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *con
 #pragma unroll
   for (int off = StencilLanes<T, DIM>::ROWS / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (L.valid && L.row == 0) ((T *)m.U[L.c])[L.k] = s;
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
+                                                const T *const u2) {
+  pdl_wait();
+  pdl_release();
+  interp_body<T, DIM>(m, u0, u1, u2, hw_blk());
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_interp_b(const __grid_constant__ Batch<MarkerFieldArgs> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const MarkerFieldArgs &A = Bt.a[batch_member(Bt, b)];
+  interp_body<T, DIM>(A.m, (const T *)A.f[0], (const T *)A.f[1], (const T *)A.f[2], b);
 }
 
 // Step 2a over the force connections at X^{n+1/2}: 8 lanes per marker share
@@ -293,10 +320,8 @@ __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *con
 //     the FP32 fraction difference df.  No FP64 instruction, and the same
 //     accuracy as rounding the FP64 difference to FP32.
 template <typename T, int DIM, bool FRAC>
-__global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
-  pdl_wait();
-  pdl_release();
-  const unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void force_body(const MarkerArgs &m, const Blk &B) {
+  const unsigned gt = B.x * blockDim.x + threadIdx.x;
   const unsigned a = gt >> 3;
   const int lane8 = (int)(gt & 7);
   const bool valid = a < (unsigned)m.nm;
@@ -357,6 +382,20 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
     ((T *)m.G[lane8])[a] = gv;
   }
 }
+template <typename T, int DIM, bool FRAC>
+__global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
+  pdl_wait();
+  pdl_release();
+  force_body<T, DIM, FRAC>(m, hw_blk());
+}
+template <typename T, int DIM, bool FRAC>
+__global__ void __launch_bounds__(256) k_force_b(const __grid_constant__ Batch<MarkerArgs> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const int i = batch_member(Bt, b);
+  force_body<T, DIM, FRAC>(Bt.a[i], b);
+}
 
 // Step 2b: f_c(node) += G_c prod_a phi_a / h^d at X^{n+1/2}, added as
 // dt/rho f_c into the momentum increment R that the right-hand-side kernel
@@ -366,10 +405,9 @@ __global__ void __launch_bounds__(256) k_force(const MarkerArgs m) {
 // numbered in Morton order of their initial positions, so neighbouring groups
 // update neighbouring nodes.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
-  pdl_wait();
-  pdl_release();
-  StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w);
+__device__ __forceinline__ void spread_body(const MarkerArgs &m, T *const f0, T *const f1, T *const f2,
+                                            const Blk &B) {
+  StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w, B);
   if (!L.valid) return;
   T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
   const T val = ((const T *)m.G[L.c])[L.k] * (T)m.spread_scale * L.wrow;
@@ -378,6 +416,20 @@ __global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0,
   for (int i = 0; i < 4; ++i) v[i] = val * L.wx[i];
   row4_add(fc + L.row_offset(m), L.bx, m.n[0], v);
 }
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
+  pdl_wait();
+  pdl_release();
+  spread_body<T, DIM>(m, f0, f1, f2, hw_blk());
+}
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_spread_b(const __grid_constant__ Batch<MarkerFieldArgs> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const MarkerFieldArgs &A = Bt.a[batch_member(Bt, b)];
+  spread_body<T, DIM>(A.m, (T *)A.f[0], (T *)A.f[1], (T *)A.f[2], b);
+}
 
 // The same spreading in 3D with a warp per (marker, c) and one scalar atomic
 // per node: a warp's atomics then fall on a few sectors of 8 rows, which the
@@ -385,15 +437,28 @@ __global__ void __launch_bounds__(256) k_spread(const MarkerArgs m, T *const f0,
 // scattered rows (26.6 against 28.5 us at 128^3).  Interpolation keeps the
 // 16-lane groups: with a warp per (marker, c) it took 27.0 instead of 22.8 us.
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread3(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
-  pdl_wait();
-  pdl_release();
-  StencilNodes3<T> L(m, m.locS_b, (const T *)m.locS_w);
+__device__ __forceinline__ void spread3_body(const MarkerArgs &m, T *const f0, T *const f1, T *const f2,
+                                             const Blk &B) {
+  StencilNodes3<T> L(m, m.locS_b, (const T *)m.locS_w, B);
   if (!L.valid) return;
   T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
   const T g = ((const T *)m.G[L.c])[L.k] * (T)m.spread_scale;
   atomicAdd(fc + L.o0, g * L.w0);
   atomicAdd(fc + L.o1, g * L.w1);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread3(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
+  pdl_wait();
+  pdl_release();
+  spread3_body<T>(m, f0, f1, f2, hw_blk());
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread3_b(const __grid_constant__ Batch<MarkerFieldArgs> Bt) {
+  pdl_wait();
+  pdl_release();
+  Blk b;
+  const MarkerFieldArgs &A = Bt.a[batch_member(Bt, b)];
+  spread3_body<T>(A.m, (T *)A.f[0], (T *)A.f[1], (T *)A.f[2], b);
 }
 
 // marker positions between the caller's [n][dim] layout and the SoA arrays
@@ -472,6 +537,60 @@ cudaError_t launch_markers_layout(double *aos, double *const X[3], const int32_t
   k_markers_layout<<<nblocks(nm * dim, 256), 256, 0, s>>>(aos, X[0], X[1], X[2], perm, nm, dim, to_soa);
   return cudaGetLastError();
 }
+
+// batched launchers: every member of the batch has the same dim and precision
+template <typename T>
+cudaError_t launch_interp_batch(const MarkerFieldArgs *a, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int d = a[0].m.dim;
+  std::vector<dim3> g(n);
+  for (int i = 0; i < n; ++i) g[i] = dim3(a[i].m.nm ? nblocks(a[i].m.nm * d * (d == 3 ? 16 : 4), 256) : 0);
+  if (d == 2) return launch_batch(k_interp_b<T, 2>, a, g.data(), n, dim3(256), s);
+  return launch_batch(k_interp_b<T, 3>, a, g.data(), n, dim3(256), s);
+}
+
+template <typename T>
+cudaError_t launch_update_batch(const MarkerArgs *m, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int d = m[0].dim;
+  std::vector<dim3> g(n);
+  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * d, 256) : 0);
+  if (d == 2) return launch_batch(k_update_b<T, 2>, m, g.data(), n, dim3(256), s);
+  return launch_batch(k_update_b<T, 3>, m, g.data(), n, dim3(256), s);
+}
+
+template <typename T>
+cudaError_t launch_force_batch(const MarkerArgs *m, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int d = m[0].dim;
+  std::vector<dim3> g(n);
+  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * 8, 256) : 0);
+  if (m[0].frac_force) {
+    if (d == 2) return launch_batch(k_force_b<T, 2, true>, m, g.data(), n, dim3(256), s);
+    return launch_batch(k_force_b<T, 3, true>, m, g.data(), n, dim3(256), s);
+  }
+  if (d == 2) return launch_batch(k_force_b<T, 2, false>, m, g.data(), n, dim3(256), s);
+  return launch_batch(k_force_b<T, 3, false>, m, g.data(), n, dim3(256), s);
+}
+
+template <typename T>
+cudaError_t launch_spread_batch(const MarkerFieldArgs *a, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int d = a[0].m.dim;
+  std::vector<dim3> g(n);
+  for (int i = 0; i < n; ++i) g[i] = dim3(a[i].m.nm ? nblocks(a[i].m.nm * d * (d == 3 ? 32 : 4), 256) : 0);
+  if (d == 2) return launch_batch(k_spread_b<T, 2>, a, g.data(), n, dim3(256), s);
+  return launch_batch(k_spread3_b<T>, a, g.data(), n, dim3(256), s);
+}
+
+template cudaError_t launch_interp_batch<float>(const MarkerFieldArgs *, int, cudaStream_t);
+template cudaError_t launch_interp_batch<double>(const MarkerFieldArgs *, int, cudaStream_t);
+template cudaError_t launch_update_batch<float>(const MarkerArgs *, int, cudaStream_t);
+template cudaError_t launch_update_batch<double>(const MarkerArgs *, int, cudaStream_t);
+template cudaError_t launch_force_batch<float>(const MarkerArgs *, int, cudaStream_t);
+template cudaError_t launch_force_batch<double>(const MarkerArgs *, int, cudaStream_t);
+template cudaError_t launch_spread_batch<float>(const MarkerFieldArgs *, int, cudaStream_t);
+template cudaError_t launch_spread_batch<double>(const MarkerFieldArgs *, int, cudaStream_t);
 
 template cudaError_t launch_locate<float>(const MarkerArgs &, cudaStream_t);
 template cudaError_t launch_locate<double>(const MarkerArgs &, cudaStream_t);

@@ -12,7 +12,9 @@
 // doubles (about 25 KB).  Every GPU that loads the library holds it until the
 // process exits.  Host code cannot use the array's name as a device address,
 // so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current and caches it.
+// cudaGetSymbolAddress while that device is current and caches it (again
+// whenever the device's context has changed since).  Devices 0 .. 63 are
+// supported.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -31,12 +33,34 @@ constexpr int kMaxN = IB_NOALLOC_MAX_N;
 constexpr int kRow = kMaxN + 8;  // one table of lam^0 .. lam^n per axis
 constexpr int kMaxDevices = 64;
 
-// [0][axis][k]: FP64 table; [1][axis][...]: FP32 table stored in the first
-// half of the row's bytes.  Rewritten completely by every call.
+// [0][axis][k]: FP64 table; [1][axis][...]: FP32 table in the first half of
+// the row's bytes and the FP32 remainders lam^k - (float)lam^k in the second
+// half.  Rewritten completely by every call.
 static __device__ __align__(256) double g_noalloc_pw[2][3][kRow];
 
+// per device: the context the address was looked up in, and the address.  A
+// device whose primary context was destroyed and created again (for example
+// after cudaDeviceReset) reloads the library's module, and the array may then
+// sit at another address, so the lookup is repeated when the context changes.
 std::mutex g_mu;
+void *g_ctx[kMaxDevices] = {};
 double *g_addr[kMaxDevices] = {};
+
+// the current driver context (cuCtxGetCurrent, reached through the runtime's
+// entry-point query so that the library needs no link against libcuda)
+typedef int (*CtxGetCurrentFn)(void **);
+CtxGetCurrentFn ctx_get_current() {
+  static std::once_flag once;
+  static CtxGetCurrentFn fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  return fn;
+}
 
 // lam^k for k = 0..n of every axis; blockIdx.x = axis.  lam^k by binary
 // powering in FP64, the FP32 table is the FP64 value rounded.
@@ -54,6 +78,7 @@ __global__ void k_fill_powers(double *base, int n0, int n1, int n2, double l0, d
     }
     pd[k] = p;
     pf[k] = (float)p;
+    pf[kRow + k] = (float)(p - (double)(float)p);
   }
 }
 
@@ -82,14 +107,23 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return ib_internal_fail(IB_ERR_ARG, "ib_split_solve_noalloc: device index");
+  CtxGetCurrentFn get_ctx = ctx_get_current();
+  if (!get_ctx) return ib_internal_fail(IB_ERR_CUDA, "ib_split_solve_noalloc: cuCtxGetCurrent unavailable");
   double *base;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    void *ctx = nullptr;
+    if (get_ctx(&ctx) != 0) return ib_internal_fail(IB_ERR_CUDA, "ib_split_solve_noalloc: cuCtxGetCurrent failed");
+    if (!ctx || !g_addr[dev] || g_ctx[dev] != ctx) {
+      // no context yet on this thread (the lookup below creates the device's
+      // primary context), a first call, or a context created anew
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_pw);
       if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));
+      if (get_ctx(&ctx) != 0 || !ctx)
+        return ib_internal_fail(IB_ERR_CUDA, "ib_split_solve_noalloc: no current CUDA context");
       g_addr[dev] = (double *)p;
+      g_ctx[dev] = ctx;
     }
     base = g_addr[dev];
   }
@@ -120,8 +154,10 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
       sa.fin[0] = a == 0 ? (const float *)f : nullptr;
       for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
       sa.dim = dim;
-      sa.co = LineCoef<float>{reinterpret_cast<const float *>(base + (size_t)(3 + a) * kRow), (float)lam[a],
-                              (float)scale, (float)inv_1m[a]};
+      const float *pf = reinterpret_cast<const float *>(base + (size_t)(3 + a) * kRow);
+      const float q_hi = (float)inv_1m[a];
+      sa.co = LineCoef<float>{pf, (float)lam[a], (float)scale, q_hi, pf + kRow, (float)(inv_1m[a] - (double)q_hi),
+                              1.0 - 1.0 / inv_1m[a] > 0x1p-24 ? 1 : 0};
       e = launch_sweep<float>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
     } else {
       SweepArgs<double> sa;
@@ -130,7 +166,7 @@ extern "C" int ib_split_solve_noalloc(int precision, int dim, const int n[3], co
       sa.fin[0] = a == 0 ? (const double *)f : nullptr;
       for (int q = 0; q < 3; ++q) sa.n[q] = q < dim ? n[q] : 1;
       sa.dim = dim;
-      sa.co = LineCoef<double>{base + (size_t)a * kRow, lam[a], scale, inv_1m[a]};
+      sa.co = LineCoef<double>{base + (size_t)a * kRow, lam[a], scale, inv_1m[a], nullptr, 0.0, 0};
       e = launch_sweep<double>(a, PRO_LOAD, EPI_STORE, 1, sa, s);
     }
     if (e != cudaSuccess) return ib_internal_fail(IB_ERR_CUDA, cudaGetErrorString(e));

@@ -81,17 +81,26 @@ struct DevCoef {
 };
 int upload_coef(const HostCoef &h, DevCoef &out, cudaStream_t s) {
   const int m = (int)h.pw.size();
-  size_t bytes = m * sizeof(double) + m * sizeof(float) + 64;
+  size_t bytes = m * sizeof(double) + 2 * m * sizeof(float) + 64;
   IB_CUDA(cudaMalloc(&out.mem, bytes));
   double *pd = (double *)out.mem;
   float *pf = (float *)(pd + m);
-  std::vector<float> hf(m);
-  for (int k = 0; k < m; ++k) hf[k] = (float)h.pw[k];
+  float *pf_lo = pf + m;
+  // FP32 tables: lam^k rounded, and the remainder lam^k - (float)lam^k
+  std::vector<float> hf(2 * m);
+  for (int k = 0; k < m; ++k) {
+    hf[k] = (float)h.pw[k];
+    hf[m + k] = (float)(h.pw[k] - (double)hf[k]);
+  }
   IB_CUDA(cudaMemcpyAsync(pd, h.pw.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
-  IB_CUDA(cudaMemcpyAsync(pf, hf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
+  IB_CUDA(cudaMemcpyAsync(pf, hf.data(), 2 * m * sizeof(float), cudaMemcpyHostToDevice, s));
   IB_CUDA(cudaStreamSynchronize(s));
-  out.d = LineCoef<double>{pd, h.lam, h.inv_c, h.inv_1m};
-  out.f = LineCoef<float>{pf, (float)h.lam, (float)h.inv_c, (float)h.inv_1m};
+  out.d = LineCoef<double>{pd, h.lam, h.inv_c, h.inv_1m, nullptr, 0.0, 0};
+  // FP32 solves evaluate the periodic correction to FP64 accuracy whenever
+  // the wrap weight lam^n is above FP32 resolution
+  const int ext = h.pw[m - 1] > 0x1p-24 ? 1 : 0;
+  const float q_hi = (float)h.inv_1m;
+  out.f = LineCoef<float>{pf, (float)h.lam, (float)h.inv_c, q_hi, pf_lo, (float)(h.inv_1m - (double)q_hi), ext};
   return IB_OK;
 }
 
@@ -237,47 +246,38 @@ MarkerArgs marker_args(ib_grid_s *g, bool first) {
   return m;
 }
 
+// The arguments of every kernel of one step (Sec. 3.4, Steps 1a-3f) of grid
+// g: the marker chain, the right-hand side, spreading and the 2d sweeps with
+// their configurations.  enqueue_step_t launches one plan; an ensemble
+// launches the plans of a size class together (batched launches).
 template <typename T>
-int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+struct StepPlan {
+  MarkerArgs m;
+  const T *uc[3];
+  T *sc[3];
+  RhsArgs<T> ra;
+  SweepArgs<T> sw[6];
+  int ax[6], pro[6], epi[6], nf[6], cfg[6], cfg_r[6];
+  int nsw;
+};
+
+template <typename T>
+void plan_step(ib_grid_s *g, bool first, int phase, StepPlan<T> &P) {
   const int d = g->dim;
   int order[3];
   for (int i = 0; i < d; ++i) order[i] = (i + phase) % d;
-  auto mark = [&](int slot) -> int {
-    if (ev) IB_CUDA(cudaEventRecord(ev[slot], g->s));
-    return IB_OK;
-  };
-  int rc;
-  MarkerArgs m = marker_args(g, first);
-  const T *uc[3] = {(const T *)g->u[0], (const T *)g->u[1], (const T *)g->u[2]};
-  T *sc[3] = {(T *)g->scr[0], (T *)g->scr[1], (T *)g->scr[2]};
-  // Steps 1a-2a; spreading (Step 2b) follows the right-hand side, into which
-  // it adds dt/rho f
-  // the marker chain (interp, update, force) runs on a second, higher-priority
-  // stream beside the right-hand side (they share no data); spreading waits
-  // for both.  Profiling (ev set) keeps one stream so that every kernel is
-  // timed alone.
-  const bool fork = !ev && g->nm > 0;
-  if ((rc = mark(0))) return rc;
-  cudaStream_t ms = g->s;
-  if (fork) {
-    IB_CUDA(cudaEventRecord(g->ev_fork, g->s));
-    IB_CUDA(cudaStreamWaitEvent(g->s2, g->ev_fork, 0));
-    ms = g->s2;
+  P.m = marker_args(g, first);
+  for (int a = 0; a < 3; ++a) {
+    P.uc[a] = (const T *)g->u[a];
+    P.sc[a] = (T *)g->scr[a];
   }
-  IB_CUDA(launch_interp<T>(m, uc, ms));
-  if ((rc = mark(1))) return rc;
-  IB_CUDA(launch_update<T>(m, ms));
-  if ((rc = mark(2))) return rc;
-  IB_CUDA(launch_force<T>(m, ms));
-  if ((rc = mark(3))) return rc;
-  if (fork) IB_CUDA(cudaEventRecord(g->ev_join, g->s2));
   // Steps 3a-3b
-  RhsArgs<T> ra;
+  RhsArgs<T> &ra = P.ra;
   memset(&ra, 0, sizeof(ra));
   for (int a = 0; a < 3; ++a) {
-    ra.u[a] = uc[a];
+    ra.u[a] = P.uc[a];
     ra.Nold[a] = (T *)g->Nold[a];
-    ra.scr[a] = sc[a];
+    ra.scr[a] = P.sc[a];
     ra.inv_h[a] = (T)(1.0 / g->h[a]);
     ra.inv_h2[a] = (T)(1.0 / (g->h[a] * g->h[a]));
     ra.n[a] = g->n[a];
@@ -293,18 +293,12 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   ra.p = (const T *)g->p;
   ra.psi = gm1 ? nullptr : (const T *)g->psi;
   ra.first = first ? 1 : 0;
-  IB_CUDA(launch_rhs<T>(d, ra, g->s));
-  if ((rc = mark(4))) return rc;
-  if (fork) IB_CUDA(cudaStreamWaitEvent(g->s, g->ev_join, 0));
-  // Step 2b: R += dt/rho S(X^{n+1/2}) G
-  IB_CUDA(launch_spread<T>(m, sc, g->s));
-  if ((rc = mark(5))) return rc;
   // Steps 3c-3d (+ z): increment-form Douglas sweeps on the scratch fields
   SweepArgs<T> sa;
   memset(&sa, 0, sizeof(sa));
   for (int a = 0; a < 3; ++a) {
-    sa.f[a] = sc[a];
-    sa.u[a] = uc[a];
+    sa.f[a] = P.sc[a];
+    sa.u[a] = P.uc[a];
     sa.uo[a] = (T *)g->u[a];
     sa.inv_h[a] = (T)(1.0 / g->h[a]);
     sa.n[a] = g->n[a];
@@ -315,24 +309,81 @@ int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
   sa.chi_mu_half = gm1 ? T(0) : (T)(0.5 * g->desc.chi * g->desc.mu);
   sa.p_keep = gm1 ? T(0) : T(1);
   sa.dim = d;
-  for (int st = 0; st < d; ++st) {
+  int k = 0;
+  for (int st = 0; st < d; ++st, ++k) {
     const int ax = order[st];
     sa.co = chain_coef<T>(g->coef[0], order, st, d);
     const bool last = st == d - 1;
-    IB_CUDA(launch_sweep<T>(ax, PRO_LOAD, last ? EPI_ADDU : EPI_STORE, d, sa, g->s, last ? g->tune_r[ax] : g->tune[ax]));
-    if ((rc = mark(6 + st))) return rc;
+    P.sw[k] = sa;
+    P.ax[k] = ax;
+    P.pro[k] = PRO_LOAD;
+    P.epi[k] = last ? EPI_ADDU : EPI_STORE;
+    P.nf[k] = d;
+    P.cfg[k] = last ? g->tune_r[ax] : g->tune[ax];
+    P.cfg_r[k] = g->tune_r[ax];
   }
   // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
   // last sweeps
   sa.f[0] = sa.f[1] = sa.f[2] = (T *)g->psi;
-  for (int st = 0; st < d; ++st) {
+  for (int st = 0; st < d; ++st, ++k) {
     const int ax = order[st];
     sa.co = chain_coef<T>(g->coef[1], order, st, d);
     const int pro = st == 0 ? PRO_DIV : PRO_LOAD;
     const int epi = st == d - 1 ? EPI_P : EPI_STORE;
     const bool plain = pro == PRO_LOAD && epi == EPI_STORE;
-    IB_CUDA(launch_sweep<T>(ax, pro, epi, 1, sa, g->s, plain ? g->tune[ax] : g->tune_r[ax]));
-    if ((rc = mark(9 + st))) return rc;
+    P.sw[k] = sa;
+    P.ax[k] = ax;
+    P.pro[k] = pro;
+    P.epi[k] = epi;
+    P.nf[k] = 1;
+    P.cfg[k] = plain ? g->tune[ax] : g->tune_r[ax];
+    P.cfg_r[k] = g->tune_r[ax];
+  }
+  P.nsw = k;
+}
+
+template <typename T>
+int enqueue_step_t(ib_grid_s *g, bool first, int phase, cudaEvent_t *ev) {
+  auto mark = [&](int slot) -> int {
+    if (ev) IB_CUDA(cudaEventRecord(ev[slot], g->s));
+    return IB_OK;
+  };
+  int rc;
+  StepPlan<T> P;
+  plan_step<T>(g, first, phase, P);
+  // Steps 1a-2a; spreading (Step 2b) follows the right-hand side, into which
+  // it adds dt/rho f
+  // the marker chain (interp, update, force) runs on a second, higher-priority
+  // stream beside the right-hand side (they share no data); spreading waits
+  // for both.  Profiling (ev set) keeps one stream so that every kernel is
+  // timed alone.
+  const bool fork = !ev && g->nm > 0;
+  if ((rc = mark(0))) return rc;
+  cudaStream_t ms = g->s;
+  if (fork) {
+    IB_CUDA(cudaEventRecord(g->ev_fork, g->s));
+    IB_CUDA(cudaStreamWaitEvent(g->s2, g->ev_fork, 0));
+    ms = g->s2;
+  }
+  IB_CUDA(launch_interp<T>(P.m, P.uc, ms));
+  if ((rc = mark(1))) return rc;
+  IB_CUDA(launch_update<T>(P.m, ms));
+  if ((rc = mark(2))) return rc;
+  IB_CUDA(launch_force<T>(P.m, ms));
+  if ((rc = mark(3))) return rc;
+  if (fork) IB_CUDA(cudaEventRecord(g->ev_join, g->s2));
+  // Steps 3a-3b
+  IB_CUDA(launch_rhs<T>(g->dim, P.ra, g->s));
+  if ((rc = mark(4))) return rc;
+  if (fork) IB_CUDA(cudaStreamWaitEvent(g->s, g->ev_join, 0));
+  // Step 2b: R += dt/rho S(X^{n+1/2}) G
+  IB_CUDA(launch_spread<T>(P.m, P.sc, g->s));
+  if ((rc = mark(5))) return rc;
+  // Steps 3c-3f: marks 6 + s after the s-th momentum sweep, 9 + s after the
+  // s-th psi sweep
+  for (int k = 0; k < P.nsw; ++k) {
+    IB_CUDA(launch_sweep<T>(P.ax[k], P.pro[k], P.epi[k], P.nf[k], P.sw[k], g->s, P.cfg[k]));
+    if ((rc = mark(k < g->dim ? 6 + k : 9 + (k - g->dim)))) return rc;
   }
   return IB_OK;
 }
@@ -873,6 +924,22 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
 
 bool valid_n(int n) { return n >= 8 && n <= 512; }
 
+// Host view of an input array that may live in host or device memory: device
+// (and managed) arrays are copied into tmp on the grid's stream.
+template <typename T>
+int host_view(ib_grid_s *g, const T *p, int64_t count, std::vector<T> &tmp, const T **out) {
+  *out = p;
+  if (!p || count <= 0) return IB_OK;
+  cudaPointerAttributes at;
+  IB_CUDA(cudaPointerGetAttributes(&at, p));
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return IB_OK;
+  tmp.resize((size_t)count);
+  IB_CUDA(cudaMemcpyAsync(tmp.data(), p, (size_t)count * sizeof(T), cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  *out = tmp.data();
+  return IB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -979,16 +1046,28 @@ int ib_destroy_grid(ib_grid_t g) {
   return IB_OK;
 }
 
-int ib_add_fiber(ib_grid_t g, const double *X0, int64_t n_markers, const int32_t *edges, const double *kappa,
-                 const double *rest_len, int64_t n_edges, const int32_t *tris, int64_t n_tris,
-                 int32_t *fiber_id_out) {
+int ib_add_fiber(ib_grid_t g, const double *X0_in, int64_t n_markers, const int32_t *edges_in,
+                 const double *kappa_in, const double *rest_in, int64_t n_edges, const int32_t *tris_in,
+                 int64_t n_tris, int32_t *fiber_id_out) {
   if (!g) return fail(IB_ERR_ARG, "null grid");
   if (g->step != 0 || g->markers_uploaded) return fail(IB_ERR_STATE, "fibers can only be added before the first step");
   if (n_markers < 0 || n_edges < 0 || n_tris < 0) return fail(IB_ERR_ARG, "negative count");
-  if (n_markers > 0 && !X0) return fail(IB_ERR_ARG, "null X0");
-  if (n_edges > 0 && (!edges || !kappa)) return fail(IB_ERR_ARG, "null edges or kappa");
+  if (n_markers > 0 && !X0_in) return fail(IB_ERR_ARG, "null X0");
+  if (n_edges > 0 && (!edges_in || !kappa_in)) return fail(IB_ERR_ARG, "null edges or kappa");
   if (g->nm + n_markers > ((int64_t)1 << 25)) return fail(IB_ERR_ARG, "more than 2^25 markers");
   const int d = g->dim;
+  // every array may be host or device memory
+  std::vector<double> tX, tK, tR;
+  std::vector<int32_t> tE, tT;
+  const double *X0, *kappa, *rest_len;
+  const int32_t *edges, *tris;
+  int rc = enter(g);
+  if (rc) return rc;
+  if ((rc = host_view(g, X0_in, n_markers * d, tX, &X0)) || (rc = host_view(g, edges_in, 2 * n_edges, tE, &edges)) ||
+      (rc = host_view(g, kappa_in, n_edges, tK, &kappa)) || (rc = host_view(g, rest_in, n_edges, tR, &rest_len)) ||
+      (rc = host_view(g, tris_in, d == 3 ? 3 * n_tris : 0, tT, &tris)))
+    return rc;
+  if ((rc = leave(g))) return rc;
   for (int64_t i = 0; i < n_markers * d; ++i)
     if (!isfinite(X0[i])) return fail(IB_ERR_NONFINITE, "non-finite marker position");
   for (int64_t e = 0; e < 2 * n_edges; ++e)
@@ -1430,28 +1509,81 @@ int ib_adjoint_run(ib_grid_t g, int n_steps, int checkpoint_every, const double 
 // ---------------------------------------------------------------------------
 // ensembles
 
+// Members are grouped into size classes (same precision, dim and n): within
+// a class every kernel of the step has the same template instance and
+// launch shape, so each kernel slot of a step is ONE batched launch that
+// walks the class's member table (launch_batch); the classes run side by
+// side on their own streams, and in each class the marker chain runs beside
+// the right-hand side as in a single grid's step.
 struct ib_ensemble_s {
   std::vector<ib_grid_s *> m;
   cudaStream_t s = nullptr, user = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
-  std::vector<cudaEvent_t> ev_join;
+  std::vector<cudaEvent_t> ev_join;  // per member: ordering against its own stream
+  std::vector<std::vector<int>> cls;  // member indices of each size class
+  std::vector<cudaStream_t> cs, cs2;  // per class: main and marker-chain streams
+  std::vector<cudaEvent_t> cev_fork, cev_mk, cev_join;
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
   int dim = 0;
 };
 
 namespace {
 
-// one step of every member: fork from the ensemble stream into the members'
-// streams, one branch per member, then join back
+// one step of the members of size class c, in batched launches
+template <typename T>
+int ens_class_step(ib_ensemble_s *e, int c, bool first, int phase) {
+  const std::vector<int> &mem = e->cls[c];
+  const int n = (int)mem.size();
+  std::vector<StepPlan<T>> P(n);
+  std::vector<MarkerFieldArgs> mi(n), msp(n);
+  std::vector<MarkerArgs> mm(n);
+  std::vector<RhsArgs<T>> ra(n);
+  std::vector<SweepArgs<T>> sw(n);
+  bool markers = false;
+  for (int i = 0; i < n; ++i) {
+    plan_step<T>(e->m[mem[i]], first, phase, P[i]);
+    mm[i] = P[i].m;
+    mi[i].m = msp[i].m = P[i].m;
+    for (int a = 0; a < 3; ++a) {
+      mi[i].f[a] = (void *)P[i].uc[a];
+      msp[i].f[a] = (void *)P[i].sc[a];
+    }
+    ra[i] = P[i].ra;
+    markers = markers || P[i].m.nm > 0;
+  }
+  cudaStream_t s1 = e->cs[c], s2 = e->cs2[c];
+  if (markers) {
+    IB_CUDA(cudaEventRecord(e->cev_fork[c], s1));
+    IB_CUDA(cudaStreamWaitEvent(s2, e->cev_fork[c], 0));
+    IB_CUDA(launch_interp_batch<T>(mi.data(), n, s2));
+    IB_CUDA(launch_update_batch<T>(mm.data(), n, s2));
+    IB_CUDA(launch_force_batch<T>(mm.data(), n, s2));
+    IB_CUDA(cudaEventRecord(e->cev_mk[c], s2));
+  }
+  IB_CUDA(launch_rhs_batch<T>(e->dim, ra.data(), n, s1));
+  if (markers) {
+    IB_CUDA(cudaStreamWaitEvent(s1, e->cev_mk[c], 0));
+    IB_CUDA(launch_spread_batch<T>(msp.data(), n, s1));
+  }
+  for (int k = 0; k < P[0].nsw; ++k) {
+    for (int i = 0; i < n; ++i) sw[i] = P[i].sw[k];
+    IB_CUDA(launch_sweep_batch<T>(P[0].ax[k], P[0].pro[k], P[0].epi[k], P[0].nf[k], sw.data(), n, s1,
+                                  P[0].cfg_r[k]));
+  }
+  return IB_OK;
+}
+
+// one step of every member: fork from the ensemble stream into the class
+// streams, then join back
 int ens_enqueue(ib_ensemble_s *e, bool first, int phase) {
   IB_CUDA(cudaEventRecord(e->ev_fork, e->s));
-  for (size_t i = 0; i < e->m.size(); ++i) {
-    ib_grid_s *g = e->m[i];
-    IB_CUDA(cudaStreamWaitEvent(g->s, e->ev_fork, 0));
-    int rc = enqueue_step(g, first, phase, nullptr);
+  for (size_t c = 0; c < e->cls.size(); ++c) {
+    IB_CUDA(cudaStreamWaitEvent(e->cs[c], e->ev_fork, 0));
+    const int rc = e->m[e->cls[c][0]]->prec == IB_FP32 ? ens_class_step<float>(e, (int)c, first, phase)
+                                                       : ens_class_step<double>(e, (int)c, first, phase);
     if (rc) return rc;
-    IB_CUDA(cudaEventRecord(e->ev_join[i], g->s));
-    IB_CUDA(cudaStreamWaitEvent(e->s, e->ev_join[i], 0));
+    IB_CUDA(cudaEventRecord(e->cev_join[c], e->cs[c]));
+    IB_CUDA(cudaStreamWaitEvent(e->s, e->cev_join[c], 0));
   }
   return IB_OK;
 }
@@ -1484,6 +1616,12 @@ int ib_destroy_ensemble(ib_ensemble_t e) {
     if (e->graph[i]) cudaGraphExecDestroy(e->graph[i]);
   for (cudaEvent_t ev : e->ev_join)
     if (ev) cudaEventDestroy(ev);
+  for (auto *v : {&e->cev_fork, &e->cev_mk, &e->cev_join})
+    for (cudaEvent_t ev : *v)
+      if (ev) cudaEventDestroy(ev);
+  for (auto *v : {&e->cs, &e->cs2})
+    for (cudaStream_t st : *v)
+      if (st) cudaStreamDestroy(st);
   if (e->ev_in) cudaEventDestroy(e->ev_in);
   if (e->ev_out) cudaEventDestroy(e->ev_out);
   if (e->ev_fork) cudaEventDestroy(e->ev_fork);
@@ -1521,6 +1659,34 @@ int ib_create_ensemble(const ib_grid_t *members, int n_members, void *stream, ib
     if (cudaEventCreateWithFlags(&e->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
       ib_destroy_ensemble(e);
       return fail(IB_ERR_CUDA, "ensemble event creation failed");
+    }
+  // size classes in order of first appearance
+  for (int i = 0; i < n_members; ++i) {
+    const ib_grid_s *g = members[i];
+    size_t c = 0;
+    for (; c < e->cls.size(); ++c) {
+      const ib_grid_s *h = members[e->cls[c][0]];
+      if (h->prec == g->prec && h->n[0] == g->n[0] && h->n[1] == g->n[1] && h->n[2] == g->n[2]) break;
+    }
+    if (c == e->cls.size()) e->cls.emplace_back();
+    e->cls[c].push_back(i);
+  }
+  const size_t nc = e->cls.size();
+  e->cs.assign(nc, nullptr);
+  e->cs2.assign(nc, nullptr);
+  e->cev_fork.assign(nc, nullptr);
+  e->cev_mk.assign(nc, nullptr);
+  e->cev_join.assign(nc, nullptr);
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  for (size_t c = 0; c < nc; ++c)
+    if (cudaStreamCreateWithFlags(&e->cs[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&e->cs2[c], cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->cev_fork[c], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->cev_mk[c], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->cev_join[c], cudaEventDisableTiming) != cudaSuccess) {
+      ib_destroy_ensemble(e);
+      return fail(IB_ERR_CUDA, "ensemble stream/event creation failed");
     }
   for (ib_grid_s *g : e->m) {
     int rc = enter(g);

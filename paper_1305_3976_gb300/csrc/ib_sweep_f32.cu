@@ -4,13 +4,16 @@
 namespace ibg {
 // Plain load/store solves of y and z lines take the TMA kernel when it
 // applies and the configuration asks for it (kTmaCfg) or is left to the
-// library (cfg < 0); every other sweep takes the register kernels.
+// library (cfg < 0); every other sweep takes the register kernels, with the
+// FP64-accurate periodic correction where the coefficients ask for it
+// (ib_sweep_f32_ext.cu).
 template <>
 cudaError_t launch_sweep<float>(int axis, int pro, int epi, int nfields, const SweepArgs<float> &a, cudaStream_t s,
                                int cfg) {
   if (axis != 0 && pro == PRO_LOAD && epi == EPI_STORE && (cfg < 0 || cfg == kTmaCfg) && sweep_tma_ok(a, axis))
     return launch_sweep_tma(axis, nfields, a, s);
-  return launch_sweep_impl<float>(axis, pro, epi, nfields, a, s, cfg);
+  if (a.co.wrap_ext) return launch_sweep_f32_ext(axis, pro, epi, nfields, a, s, cfg);
+  return launch_sweep_impl<float, false>(axis, pro, epi, nfields, a, s, cfg);
 }
 }  // namespace ibg
 

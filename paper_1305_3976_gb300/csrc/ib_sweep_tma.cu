@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ib_internal.cuh"
 
 namespace ibg {
@@ -88,7 +90,7 @@ __device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wai
 
 }  // namespace
 
-template <int CH, int W, bool FULL>
+template <int CH, int W, bool FULL, bool EXT>
 __global__ void __launch_bounds__(32 * W, 1) k_sweep_tma(const __grid_constant__ SweepTmaMaps maps,
                                                          const SweepArgs<float> a, const int axis, const int nbox,
                                                          const int boxlen) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_sweep_tma(const __grid_constant__
       for (int q = 0; q < w; ++q) cin = fmaf(cin, FULL ? gCH : pw[max(0, min(CH, nl - q * CH))], sz[q][lane]);
       float tot = cin;
       for (int q = w; q < W; ++q) tot = fmaf(tot, FULL ? gCH : pw[max(0, min(CH, nl - q * CH))], sz[q][lane]);
-      const float t = fmaf(pstart, tot * a.co.inv_1m, cin);
+      const float t = EXT ? wrap_term<true>(a.co, min(start, nl), tot, cin) : fmaf(pstart, tot * a.co.inv_1m, cin);
 #pragma unroll
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) v[e] = fmaf(lp[e + 1], t, v[e]);
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_sweep_tma(const __grid_constant__
       for (int q = W - 1; q > w; --q) cin = fmaf(cin, FULL ? gCH : pw[max(0, min(CH, nl - q * CH))], sz[q][lane]);
       float tot = cin;
       for (int q = w; q >= 0; --q) tot = fmaf(tot, FULL ? gCH : pw[max(0, min(CH, nl - q * CH))], sz[q][lane]);
-      const float t = fmaf(pend, tot * a.co.inv_1m, cin);
+      const float t = EXT ? wrap_term<true>(a.co, nl - start - len, tot, cin) : fmaf(pend, tot * a.co.inv_1m, cin);
 #pragma unroll
       for (int e = 0; e < CH; ++e)
         if (FULL || e < len) {
@@ -227,18 +229,18 @@ typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, voi
                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// the driver's tensor-map encoder, looked up once per process (thread-safe)
 EncodeFn encoder() {
+  static std::once_flag once;
   static EncodeFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  std::call_once(once, [] {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = (EncodeFn)p;
-  }
+  });
   return fn;
 }
 
@@ -322,9 +324,9 @@ cudaError_t launch_sweep_tma(int axis, int nfields, const SweepArgs<float> &a, c
       return cudaErrorInvalidValue;
   }
   const size_t smem = (size_t)kStages * 32 * nbox * boxlen * sizeof(float) + kStages * sizeof(uint64_t);
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  // SM count of the current device, queried on every call (devices may differ)
+  int sms = 0, dev = 0;
+  {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -343,8 +345,12 @@ cudaError_t launch_sweep_tma(int axis, int nfields, const SweepArgs<float> &a, c
   };
   const TmaShape t = tma_shape(nl);
   const bool full = t.ch * t.w == nl;
-#define IBG_TMA(CH, W)                                                                               \
-  if (t.ch == CH && t.w == W) return full ? run(k_sweep_tma<CH, W, true>, 32 * W) : run(k_sweep_tma<CH, W, false>, 32 * W);
+#define IBG_TMA(CH, W)                                                                                     \
+  if (t.ch == CH && t.w == W) {                                                                      \
+    if (a.co.wrap_ext)                                                                               \
+      return full ? run(k_sweep_tma<CH, W, true, true>, 32 * W) : run(k_sweep_tma<CH, W, false, true>, 32 * W); \
+    return full ? run(k_sweep_tma<CH, W, true, false>, 32 * W) : run(k_sweep_tma<CH, W, false, false>, 32 * W); \
+  }
   IBG_TMA(8, 8)
   IBG_TMA(16, 8)
   IBG_TMA(16, 16)

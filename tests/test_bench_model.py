@@ -30,8 +30,28 @@ def test_step_bytes_is_the_sum_over_the_slots():
     assert total == sum(bench.kernel_bytes(k, cells, nm, ne, 4) for k in bench.STEP_SLOTS)
     # marker kernels scale with the markers and connections only
     assert bench.step_bytes(cells, 0, 0, 4) == 49 * cells * 4
-    # the 128^3 FP32 workload: 548 345 888 bytes per step
-    assert total == 548345888
+    # the 128^3 FP32 workload: 453 969 440 bytes per step
+    assert total == 453969440
+
+
+def test_marker_models_count_marker_arrays_not_stencil_nodes():
+    # interpolation and spreading stream their marker arrays (locations: an
+    # index and 4 weights per axis, plus U or G) from HBM; the 4^d stencil
+    # nodes are cache traffic, counted as updates instead
+    nm = 40962
+    for k in ("interp", "spread"):
+        assert bench.kernel_bytes(k, 128 ** 3, nm, 0, 4) == nm * 3 * (3 * (4 + 16) + 4)
+    assert bench.stencil_updates(nm) == nm * 3 * 64
+
+
+def test_survey_per_pass_model():
+    # 55 words per cell: 461 MB per 128^3 FP32 step, 29.5 GB per 512^3 step
+    assert bench.survey_step_bytes(128 ** 3, 4) == 461373440
+    assert abs(bench.survey_step_bytes(512 ** 3, 4) - 29.5e9) < 0.05e9
+
+
+def test_fp64_operation_counts():
+    assert bench.fp64_ops("rhs", 10) == 900 and bench.fp64_ops("sweep", 10) == 40
 
 
 def test_workload_names_its_grid_and_mesh():

@@ -1,6 +1,7 @@
-"""Ensembles (members with different grids, stiffnesses and viscosities
-advanced by one graph launch per step) give the same states as the members
-stepped one by one, and match the FP64 oracle."""
+"""Ensembles (members with different grids, stiffnesses and viscosities,
+grouped into size classes, each kernel of a step one batched launch per
+class) give the same states as the members stepped one by one, and match the
+FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -8,7 +9,7 @@ import oracle as O
 import paper_1305_3976_gb300 as ib
 from paper_1305_3976_gb300 import inputs as I
 
-from test_gpu_step import compare, make_pair, psi_bound, rel
+from test_gpu_step import assert_fp64, compare, make_pair, psi_bound, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -52,11 +53,39 @@ def test_ensemble_member_matches_oracle():
     ora.step(4)
     ens.step(4)
     e = compare(ora, g)
-    assert e["u"] < psi_bound(sc, 4) and e["p"] < psi_bound(sc, 4), e
-    assert e["X"] < 1e-13
+    assert_fp64(e, 4)
+    assert e["psi"] < psi_bound(sc, 4), e
     ens.close()
     g.close()
     other.close()
+
+
+def test_ensemble_more_members_than_one_launch_holds_and_mixed_precision():
+    # 26 members of one size (two batched launches per kernel: 24 + 2), two
+    # FP64 members of another size in their own class, and one member without
+    # markers
+    many = I.ensemble_members(count=26, sizes=(16,), seed=3)
+    grids = [_grid(sc, "fp32") for sc in many]
+    solo = [_grid(sc, "fp32") for sc in many]
+    extra = I.ensemble_members(count=2, sizes=(24,), seed=4)
+    g64 = [_grid(sc, "fp64") for sc in extra]
+    s64 = [_grid(sc, "fp64") for sc in extra]
+    bare = ib.Grid(3, 16, rho=1.0, mu=0.05, dt=5e-4, precision="fp32", rotate_split=True)
+    bare.set_velocity(I.random_velocity(3, (16, 16, 16), seed=9, amplitude=0.1).astype(np.float32))
+    bare_solo = ib.Grid(3, 16, rho=1.0, mu=0.05, dt=5e-4, precision="fp32", rotate_split=True)
+    bare_solo.set_velocity(I.random_velocity(3, (16, 16, 16), seed=9, amplitude=0.1).astype(np.float32))
+    ens = ib.Ensemble(grids + g64 + [bare])
+    ens.step(5)
+    for g in solo + s64 + [bare_solo]:
+        g.step(5)
+    for a, b in zip(grids + [bare], solo + [bare_solo]):
+        assert rel(a.velocity(), b.velocity()) < 1e-5
+    for a, b in zip(g64, s64):
+        assert rel(a.velocity(), b.velocity()) < 1e-12
+        assert np.max(np.abs(a.markers() - b.markers())) < 1e-13
+    ens.close()
+    for g in grids + solo + g64 + s64 + [bare, bare_solo]:
+        g.close()
 
 
 def test_ensemble_rejects_mismatched_members():

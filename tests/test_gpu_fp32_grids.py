@@ -4,8 +4,9 @@
     random velocity field so every periodic neighbour carries data;
   - long x rows (n_x = 256 with a membrane, n_x = 512);
   - the first-order variant (p* = p, psi unused).
-FP32 tolerances: 1e-4 relative velocity and pressure (as for the other FP32
-comparisons with the FP64 oracle), markers 1e-6 h.
+FP32 tolerances: the stated targets, 1e-5 relative velocity (norm-wise and
+element-wise) and 1e-6 h markers, pressure within the bound that the FP32
+psi solve gives (fp32_bounds in tests/test_gpu_step.py).
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ import oracle as O
 import paper_1305_3976_gb300 as ib
 from paper_1305_3976_gb300 import inputs as I
 
-from test_gpu_step import compare, make_pair, small_ellipsoid
+from test_gpu_step import assert_fp32, compare, make_pair, small_ellipsoid
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +33,7 @@ def test_ragged_sizes_fluid_only(n):
     for k in (1, 3):
         ora.step(k)
         g.step(k)
-        e = compare(ora, g)
-        assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+        assert_fp32(compare(ora, g), 1.0 / max(n), ora.n)
     assert g.diagnostics()["step"] == 4
     g.close()
 
@@ -46,9 +46,7 @@ def test_wide_rows_with_membrane():
     ora, g = make_pair(sc, "fp32", u0=u0)
     ora.step(2)
     g.step(2)
-    e = compare(ora, g)
-    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
-    assert e["X"] < 1e-6 / 24, e
+    assert_fp32(compare(ora, g), 1.0 / 24, 2)
     g.close()
 
 
@@ -61,19 +59,17 @@ def test_first_order_variant_fp32():
     g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
     ora.step(4)
     g.step(4)
-    e = compare(ora, g)
-    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
+    assert_fp32(compare(ora, g), 1.0 / 32, 4)
     g.close()
 
 
 def test_rows_of_512():
     # the psi operator along x has condition number up to 1 + 4 * 512^2, so
-    # FP32 pressure carries more rounding here (measured 2e-4)
+    # FP32 pressure carries more rounding here (measured 2.3e-4 to 3.7e-4)
     sc = fluid_scene((512, 8, 8))
     u0 = I.random_velocity(3, sc.n, seed=5, amplitude=0.3)
     ora, g = make_pair(sc, "fp32", u0=u0)
     ora.step(2)
     g.step(2)
-    e = compare(ora, g)
-    assert e["u"] < 1e-4 and e["p"] < 1e-3, e
+    assert_fp32(compare(ora, g), 1.0 / 512, 2)
     g.close()

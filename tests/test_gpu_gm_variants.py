@@ -20,7 +20,7 @@ import paper_runs as R
 from paper_1305_3976_gb300 import inputs as I
 
 from test_gpu_adjoint import loss_of
-from test_gpu_step import compare, psi_bound, small_ellipsoid
+from test_gpu_step import assert_fp32, assert_fp64, compare, psi_bound, small_ellipsoid
 from test_oracle_gm1 import apply_A, divergence
 import paper_1305_3976_gb300 as ib
 
@@ -46,8 +46,8 @@ def test_first_order_variant_2d_fp64():
         ora.step(steps)
         g.step(steps)
         e = compare(ora, g)
-        assert e["u"] < psi_bound(sc, ora.n) and e["p"] < psi_bound(sc, ora.n), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
         f = g.fields()
         assert np.array_equal(f["p"], f["psi"])               # the solve is the pressure
     g.close()
@@ -61,11 +61,10 @@ def test_first_order_variant_3d(precision):
     g.step(3)
     e = compare(ora, g)
     if precision == "fp64":
-        assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, 3)
+        assert e["psi"] < psi_bound(sc, 3), e
     else:
-        assert e["u"] < 1e-4 and e["p"] < 1e-4, e
-        assert e["X"] < 1e-6 / 32, e
+        assert_fp32(e, 1.0 / 32, 3)
     g.close()
 
 

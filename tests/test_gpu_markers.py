@@ -12,7 +12,8 @@ periodic wrap of unwrapped positions:
     [n, 2n): wrapped on loads and stores, the results match the untranslated
     oracle run to rounding);
   - a 2D fiber straddling the periodic boundary in both directions.
-Tolerances as in tests/test_gpu_step.py.
+Tolerances: the stated targets (assert_fp64 / assert_fp32 in
+tests/test_gpu_step.py).
 """
 import numpy as np
 import pytest
@@ -21,7 +22,7 @@ import oracle as O
 import paper_1305_3976_gb300 as ib
 from paper_1305_3976_gb300 import inputs as I
 
-from test_gpu_step import compare, psi_bound, small_ellipsoid
+from test_gpu_step import assert_fp32, assert_fp64, compare, fp32_bounds, psi_bound, record, rel, rel_max, small_ellipsoid
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +48,8 @@ def test_scattered_markers_direct_path(dim):
     sc = I.Scene(dim=dim, n=(n,) * dim, rho=1.0, mu=0.05, dt=2e-4, steps=3, X=X, edges=edges,
                  kappa=np.full(699, 0.5), rest=np.zeros(699))
     e = run_pair(sc, 3)
-    assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
-    assert e["X"] < 1e-13, e
+    assert_fp64(e, 3)
+    assert e["psi"] < psi_bound(sc, 3), e
 
 
 def test_scattered_markers_fp32_3d():
@@ -58,25 +59,23 @@ def test_scattered_markers_fp32_3d():
     edges = np.stack([np.arange(699), np.arange(1, 700)], axis=1).astype(np.int32)
     sc = I.Scene(dim=3, n=(n,) * 3, rho=1.0, mu=0.05, dt=2e-4, steps=3, X=X, edges=edges,
                  kappa=np.full(699, 0.5), rest=np.zeros(699))
-    e = run_pair(sc, 3, "fp32")
-    assert e["u"] < 1e-5, e
-    assert e["X"] < 1e-6 / n, e
+    assert_fp32(run_pair(sc, 3, "fp32"), 1.0 / n, 3)
 
 
 def test_membrane_one_period_away():
     sc = small_ellipsoid(n=32, nu=8)
     sc.X = sc.X + np.array([1.0, 0.0, -1.0])
     e = run_pair(sc, 3)
-    assert e["u"] < psi_bound(sc, 3) and e["p"] < psi_bound(sc, 3), e
-    assert e["X"] < 1e-13, e
+    assert_fp64(e, 3)
+    assert e["psi"] < psi_bound(sc, 3), e
 
 
 def test_fiber_across_the_periodic_boundary_2d():
     sc = I.thin_ellipse_2d(n=64, ns=256)
     sc.X = sc.X + np.array([0.5, 0.5])          # centred on the corner (1, 1) of the box
     e = run_pair(sc, 5)
-    assert e["u"] < psi_bound(sc, 5) and e["p"] < psi_bound(sc, 5), e
-    assert e["X"] < 1e-13, e
+    assert_fp64(e, 5)
+    assert e["psi"] < psi_bound(sc, 5), e
 
 
 def test_fp32_matches_fp64_at_full_size():
@@ -91,6 +90,7 @@ def test_fp32_matches_fp64_at_full_size():
     u32, X32 = out["fp32"]
     u64, X64 = out["fp64"]
     assert np.linalg.norm(u32 - u64) <= 1e-5 * np.linalg.norm(u64)
+    assert np.max(np.abs(u32 - u64)) <= 1e-5 * np.max(np.abs(u64))
     assert np.max(np.abs(X32 - X64)) <= 1e-6 / 128
 
 
@@ -99,9 +99,7 @@ def test_fp32_force_from_locations_with_rest_length_and_closure():
     # locations: the cylinder's axial connections (rest length L h_r) close
     # through the periodic box, so their differences need the image shift
     sc = I.cylinder_3d(n=24, dt=2e-3)
-    e = run_pair(sc, 2, "fp32")
-    assert e["u"] < 1e-4 and e["p"] < 1e-4, e
-    assert e["X"] < 1e-6 / 24, e
+    assert_fp32(run_pair(sc, 2, "fp32"), 1.0 / 24, 2)
 
 
 def test_fp32_force_from_locations_across_the_boundary():
@@ -109,15 +107,34 @@ def test_fp32_force_from_locations_across_the_boundary():
     sc = I.tiled_ellipses_2d(tiles=2, n_per_tile=32, dt=4e-3)
     P = O.params(2, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=sc.kernel, rotate=True)
     ora = O.Simulation(P, sc.X, sc.edges, sc.kappa, sc.rest, u0=sc.extra["u0"])
-    g = ib.Grid(2, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision="fp32", kernel=sc.kernel,
-                rotate_split=True)
-    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest)
-    g.set_velocity(sc.extra["u0"])
     ora.step(110)
-    g.step(110)
-    assert g.markers()[:, 1].max() > sc.H
-    e = compare(ora, g)
-    g.close()
-    h = sc.H / sc.n[0]
-    assert e["u"] < 1e-4, e
-    assert e["X"] < 1e-4 * h, e
+    runs = []
+    for _ in range(2):
+        g = ib.Grid(2, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision="fp32",
+                    kernel=sc.kernel, rotate_split=True)
+        g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest)
+        g.set_velocity(sc.extra["u0"])
+        g.step(110)
+        assert g.markers()[:, 1].max() > sc.H
+        runs.append((compare(ora, g), g.velocity().astype(np.float64), g.markers()))
+        g.close()
+    e = runs[0][0]
+    # The markers are carried across the box by a background flow of speed 1
+    # over t = 0.44 (14 h), and the FP32 rounding differences (those of the
+    # spreading atomics' order among them) grow along the way: two FP32 runs
+    # of this test differ from each other by the same order as from the FP64
+    # oracle (measured 3e-6 - 1e-5 relative velocity over repeated runs).  The
+    # velocity bounds are therefore the stated target plus four times the
+    # measured run-to-run spread, and the marker bound is the velocity target
+    # integrated along the path (measured 5e-7 - 1.4e-6, 1.6e-5 h - 4.5e-5 h).
+    spread = rel(runs[0][1], runs[1][1])
+    spread_max = rel_max(runs[0][1], runs[1][1])
+    t = 110 * sc.dt
+    speed = float(np.max(np.abs(ora.u)))
+    b = fp32_bounds(e, sc.H / sc.n[0], 110, x_tol=1e-6 * sc.H / sc.n[0] + 1e-5 * speed * t)
+    b["u"] += 4.0 * spread
+    b["u_max"] += 4.0 * spread_max
+    record({**e, "run_to_run": spread, "run_to_run_max": spread_max}, b)
+    assert e["u"] < b["u"] and e["u_max"] < b["u_max"], (e, b, spread)
+    assert e["p"] < b["p"] and e["p_max"] < b["p"], (e, b)
+    assert e["X"] < b["X"], (e, b)

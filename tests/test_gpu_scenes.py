@@ -5,15 +5,20 @@
   closed through the periodic box);
 - tiled thin ellipses in a background flow (Sec. 6.3) on the box [0, 2]^2,
   run until markers cross the periodic boundary;
-and the FP32 path at the full 128^3 benchmark size.
-Tolerances: see tests/test_gpu_step.py.
+and the FP32 path at the full 128^3 benchmark size: against the oracle after
+2 steps, and over the 200 steps of the benchmark configuration against the
+FP64 GPU run (itself tied to the oracle at this size over 10 steps in
+tests/test_gpu_step.py).
+Tolerances: the stated targets (assert_fp64 / assert_fp32 in
+tests/test_gpu_step.py).
 """
 import numpy as np
 import pytest
 
+import paper_1305_3976_gb300 as ib
 from paper_1305_3976_gb300 import inputs as I
 
-from test_gpu_step import compare, make_pair, psi_bound
+from test_gpu_step import assert_fp32, assert_fp64, compare, make_pair, psi_bound, rel, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +30,8 @@ def test_thick_shell_2d_fp64():
         ora.step(k)
         g.step(k)
         e = compare(ora, g)
-        assert e["u"] < psi_bound(sc, ora.n) and e["p"] < psi_bound(sc, ora.n), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
     g.close()
 
 
@@ -37,8 +42,8 @@ def test_cylinder_3d_rest_length_and_periodic_closure_fp64():
         ora.step(k)
         g.step(k)
         e = compare(ora, g)
-        assert e["u"] < psi_bound(sc, ora.n) and e["p"] < psi_bound(sc, ora.n), e
-        assert e["X"] < 1e-13, e
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
     g.close()
 
 
@@ -50,19 +55,47 @@ def test_tiled_ellipses_cross_the_periodic_boundary_fp64():
     X = g.markers()
     assert X[:, 1].max() > sc.H          # markers have left the box through the top
     e = compare(ora, g)
-    assert e["u"] < psi_bound(sc, 110) and e["p"] < psi_bound(sc, 110), e
-    assert e["X"] < 1e-12, e
+    assert_fp64(e, 110, x_tol=1e-12)
+    assert e["psi"] < psi_bound(sc, 110), e
     g.close()
 
 
 def test_fp32_full_size_ellipsoid_128():
     # FP32 fields with FP64 markers in the benchmark's configuration, against
-    # the FP64 oracle (measured: 5e-6 relative velocity, 3e-10 marker error)
+    # the FP64 oracle after 2 steps
     sc = I.ellipsoid_3d(n=128, nu=64)
     ora, g = make_pair(sc, "fp32")
     ora.step(2)
     g.step(2)
-    e = compare(ora, g)
-    assert e["u"] < 1e-4, e
-    assert e["X"] < 1e-6 / 128, e
+    assert_fp32(compare(ora, g), 1.0 / 128, 2)
     g.close()
+
+
+def test_fp32_benchmark_configuration_200_steps_vs_fp64():
+    # the benchmark configuration over its 200 steps: FP32 fields against the
+    # FP64 GPU run (same kernels, same summation structure), after 100 and
+    # 200 steps
+    sc = I.ellipsoid_3d(n=128, nu=64)
+    h = 1.0 / 128
+    grids = {}
+    for prec in ("fp64", "fp32"):
+        g = ib.Grid(3, sc.n, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, precision=prec, rotate_split=True)
+        g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+        grids[prec] = g
+    for k in (100, 100):
+        out = {}
+        for prec, g in grids.items():
+            g.step(k)
+            f = g.fields(("u", "v", "w", "p"))
+            out[prec] = (np.stack([f["u"], f["v"], f["w"]]).astype(np.float64), f["p"].astype(np.float64),
+                         g.markers())
+        (u32, p32, X32), (u64, p64, X64) = out["fp32"], out["fp64"]
+        e = {"u": rel(u32, u64), "u_max": rel_max(u32, u64), "p": rel(p32, p64), "p_max": rel_max(p32, p64),
+             "X": float(np.max(np.abs(X32 - X64))), "_N": 128, "_M": u64.size}
+        steps = grids["fp64"].diagnostics()["step"]
+        assert_fp32(e, h, steps)
+        # the pressure, which the target leaves open, stays at the velocity's
+        # level in this relaxation (measured 1.2e-6 after 200 steps)
+        assert e["p"] < 1e-5, e
+    for g in grids.values():
+        g.close()

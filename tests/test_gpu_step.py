@@ -14,7 +14,16 @@ psi, an increment near zero, is held to psi_bound (measured 3.9e-12 after two
 
 FP32 fields (FP64 markers): within 1e-5 relative velocity and 1e-6 h marker
 error after the 100 steps of the 2D workload (measured 1.3e-7 and 5.5e-8 h).
+
+Every field comparison is made twice: norm-wise (||a - b|| / ||b||) and
+element-wise (max |a - b| / max |b|), against the same bound.  With the
+environment variable IB_PARITY_LOG set to a file name, every checked error is
+appended to that file as one JSON line (test, errors, bound), which is where
+the measured values quoted in the docstrings come from.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -32,6 +41,22 @@ def rel(a, b):
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / (nb if nb > 0 else 1.0)
 
 
+def rel_max(a, b):
+    """max |a - b| over all elements, relative to max |b|"""
+    mb = np.max(np.abs(b)) if np.size(b) else 0.0
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / (mb if mb > 0 else 1.0)) if np.size(b) else 0.0
+
+
+def record(e, bound=None):
+    """Append the measured errors of the running test to $IB_PARITY_LOG."""
+    path = os.environ.get("IB_PARITY_LOG")
+    if not path:
+        return
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"test": test, "errors": {k: float(v) for k, v in e.items()}, "bound": bound}) + "\n")
+
+
 def make_pair(sc, precision="fp64", rotate=True, kernel=None, u0=None):
     kernel = kernel or sc.kernel
     P = O.params(sc.dim, sc.n, H=sc.H, rho=sc.rho, mu=sc.mu, dt=sc.dt, chi=sc.chi, kernel=kernel, rotate=rotate)
@@ -46,12 +71,16 @@ def make_pair(sc, precision="fp64", rotate=True, kernel=None, u0=None):
 
 
 def compare(ora, g):
+    """Errors of grid g against oracle run ora: u, p, psi norm-wise, u_max,
+    p_max element-wise (rel_max), X the largest marker difference."""
     f = g.fields()
     d = ora.P.dim
-    out = {"u": rel(np.stack([f[k] for k in ("u", "v", "w")[:d]]), ora.u),
-           "p": rel(f["p"], ora.p), "psi": rel(f["psi"], ora.psi)}
+    u = np.stack([f[k] for k in ("u", "v", "w")[:d]]).astype(np.float64)
+    out = {"u": rel(u, ora.u), "p": rel(f["p"], ora.p), "psi": rel(f["psi"], ora.psi),
+           "u_max": rel_max(u, ora.u), "p_max": rel_max(f["p"], ora.p),
+           "_N": max(ora.P.n[:d]) if hasattr(ora.P, "n") else max(u.shape[1:]), "_M": u.size}
     if ora.X.shape[0]:
-        out["X"] = np.max(np.abs(g.markers() - ora.X))
+        out["X"] = float(np.max(np.abs(g.markers() - ora.X)))
     return out
 
 
@@ -65,12 +94,48 @@ def psi_bound(sc, steps):
     return 64.0 * steps * N * EPS64 * (1 + 4.0 * N * N)
 
 
-def assert_fp64(e, steps):
-    """The FP64 targets: u and p 1e-12 relative per step, markers 1e-13
-    (absent for fluid-only runs); psi is checked against psi_bound."""
-    assert e["u"] <= 1e-12 * steps and e["p"] <= 1e-12 * steps, e
+def assert_fp64(e, steps, x_tol=1e-13):
+    """The FP64 targets: u and p within 1e-12 relative per step, norm-wise
+    and element-wise, markers within x_tol (1e-13; absent for fluid-only
+    runs); psi is checked by the caller against psi_bound."""
+    b = 1e-12 * steps
+    record(e, {"u": b, "p": b, "X": x_tol})
+    assert e["u"] <= b and e["p"] <= b, e
+    assert e["u_max"] <= b and e["p_max"] <= b, e
     if "X" in e:
-        assert e["X"] < 1e-13, e
+        assert e["X"] < x_tol, e
+
+
+EPS32 = 2.0 ** -24
+
+
+def fp32_bounds(e, h, steps, x_tol=None):
+    """The FP32 bounds (FP32 fields with FP64 markers against an FP64 run) for
+    errors e of a grid with e["_N"] cells along its longest axis and e["_M"]
+    velocity values:
+      u      1e-5 relative, norm-wise: the stated target;
+      u_max  sqrt(2 ln M) 1e-5 element-wise: the largest of M noise-like
+             errors exceeds their RMS by about sqrt(2 ln M), and
+             RMS(u) <= max |u|;
+      p      1e-4 norm-wise and element-wise for N <= 128, growing with the
+             condition number 1 + 4N^2 of the psi operator beyond (the
+             targets state no bound for the pressure; measured at most
+             3.8e-5 up to N = 128 and 3.7e-4 for rows of 512);
+      X      1e-6 h (the stated target), or x_tol where the caller states why."""
+    N = e["_N"]
+    return {"u": 1e-5, "u_max": np.sqrt(2.0 * np.log(e["_M"])) * 1e-5,
+            "p": 1e-4 * max(1.0, (1.0 + 4.0 * N * N) / (1.0 + 4.0 * 128 * 128)),
+            "X": 1e-6 * h if x_tol is None else x_tol}
+
+
+def assert_fp32(e, h, steps, x_tol=None):
+    """Check errors e (from compare, or with the same keys) against fp32_bounds."""
+    b = fp32_bounds(e, h, steps, x_tol)
+    record(e, b)
+    assert e["u"] < b["u"] and e["u_max"] < b["u_max"], (e, b)
+    assert e["p"] < b["p"] and e["p_max"] < b["p"], (e, b)
+    if "X" in e:
+        assert e["X"] < b["X"], (e, b)
 
 
 @pytest.mark.parametrize("kernel", ["peskin4", "cos4"])
@@ -114,16 +179,18 @@ def test_fp64_ragged_anisotropic_fluid_only():
     g.close()
 
 
-def test_fp64_full_size_ellipsoid_128_one_step():
+def test_fp64_full_size_ellipsoid_128_ten_steps():
     # the 128^3, nu=64 (40962-marker) membrane in the launch configuration the
-    # benchmark times; the oracle needs about 10 s for one step
+    # benchmark times, through the first-step replacements and one full
+    # rotation of the split order and beyond; the oracle needs about 2 s a step
     sc = I.ellipsoid_3d(n=128, nu=64)
     ora, g = make_pair(sc, "fp64")
-    ora.step(2)
-    g.step(2)
-    e = compare(ora, g)
-    assert_fp64(e, 2)
-    assert e["psi"] < psi_bound(sc, 2), e
+    for k in (2, 8):
+        ora.step(k)
+        g.step(k)
+        e = compare(ora, g)
+        assert_fp64(e, ora.n)
+        assert e["psi"] < psi_bound(sc, ora.n), e
     g.close()
 
 
@@ -133,10 +200,47 @@ def test_fp32_thin_ellipse_100_steps_error_vs_fp64_oracle():
     ora, g = make_pair(sc, "fp32")
     ora.step(100)
     g.step(100)
-    e = compare(ora, g)
-    h = 1.0 / 64
-    assert e["u"] < 1e-5, e
-    assert e["X"] < 1e-6 * h, e
+    assert_fp32(compare(ora, g), 1.0 / 64, 100)
+    g.close()
+
+
+def test_nonfinite_velocity_is_reported_after_a_step():
+    # one NaN cell planted in the initial velocity (host side) spreads through
+    # the step's stencils and line solves; the device-side scan of
+    # ib_diagnostics must report it
+    sc = small_ellipsoid(n=16, nu=4)
+    for prec in ("fp64", "fp32"):
+        g = ib.Grid(3, 16, precision=prec, rotate_split=True)
+        g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+        u0 = np.zeros((3, 16, 16, 16))
+        u0[1, 5, 7, 3] = np.nan
+        g.set_velocity(u0)
+        g.step(1)
+        d, rc = ib.ib_diagnostics(g.h, check=False)
+        assert rc == ib.IB_ERR_NONFINITE, (prec, rc, d)
+        with pytest.raises(ib.IBError) as ex:
+            g.diagnostics()
+        assert ex.value.code == ib.IB_ERR_NONFINITE
+        g.close()
+    # a finite state reports IB_OK
+    g = ib.Grid(3, 16, precision="fp32", rotate_split=True)
+    g.add_fiber(sc.X, sc.edges, sc.kappa, sc.rest, sc.tris)
+    g.step(2)
+    assert ib.ib_diagnostics(g.h, check=False)[1] == ib.IB_OK
+    g.close()
+
+
+def test_area_diagnostic_2d_matches_oracle_and_closed_form():
+    # 2D volume diagnostic = area enclosed by the directed fiber loops
+    # (Sec. 5.1): at n = 0 the ellipse polygon's closed form
+    # r1 r2 (ns/2) sin(2 pi/ns), after steps the oracle's area of its markers
+    sc = I.thin_ellipse_2d(n=64, ns=256)
+    ora, g = make_pair(sc, "fp64")
+    d0 = g.diagnostics()
+    assert d0["volume"] == pytest.approx(0.2 * 0.25 * 128 * np.sin(2 * np.pi / 256), rel=1e-13)
+    ora.step(20)
+    g.step(20)
+    assert g.diagnostics()["volume"] == pytest.approx(O.area_2d(ora.X, sc.edges), rel=1e-12)
     g.close()
 
 
@@ -192,3 +296,25 @@ def test_fixed_sweep_configuration_replaces_the_autotuner():
     assert ex.value.code == ib.IB_ERR_STATE
     g0.close()
     g1.close()
+
+
+def test_add_fiber_from_device_arrays():
+    # the structure passed as device arrays (torch CUDA tensors) gives the same
+    # steps as the same structure passed from host memory (to the rounding
+    # of the spreading atomics' order, which differs from run to run)
+    import torch
+
+    sc = small_ellipsoid(n=32, nu=8)
+    out = []
+    for on_device in (False, True):
+        g = ib.Grid(3, 32, rho=sc.rho, mu=sc.mu, dt=sc.dt, precision="fp64", rotate_split=True)
+        arrs = (sc.X, sc.edges.astype(np.int32), sc.kappa, sc.rest, sc.tris.astype(np.int32))
+        if on_device:
+            arrs = tuple(torch.tensor(np.ascontiguousarray(a), device="cuda") for a in arrs)
+        g.add_fiber(*arrs)
+        g.step(3)
+        out.append((g.velocity(), g.markers(), g.diagnostics()["volume"]))
+        g.close()
+    assert np.max(np.abs(out[0][1] - out[1][1])) < 1e-14
+    assert out[0][2] == pytest.approx(out[1][2], rel=1e-13)
+    assert rel(out[0][0], out[1][0]) < 1e-12
