@@ -163,12 +163,12 @@ const char *ib_last_error(void);
 
 /* Ensembles of independent grids (each with its own size, parameters and
  * structures) advanced together.  Members of the same precision and size form
- * a size class; every kernel of a step (Sec. 3.4, Steps 1a-3f) is one batched
- * launch per class that walks the class's member table (at most 24 members a
- * launch), the classes run side by side, and a whole ensemble step is one
- * CUDA graph launch.  The paper runs one problem at a time; this batches
- * many.  Within a class the line solves use the register kernels with the
- * shape the class's first member chose (ib_sweep_config), so an ensemble
+ * a size class, split into groups of at most 4; every kernel of a step
+ * (Sec. 3.4, Steps 1a-3f) is one batched launch per group that walks the
+ * group's member table, the groups run side by side, and a whole ensemble
+ * step is one CUDA graph launch.  The paper runs one problem at a time; this batches
+ * many.  Within a group the line solves use the register kernels with the
+ * shape the group's first member chose (ib_sweep_config), so an ensemble
  * member agrees with the same grid stepped alone to rounding.
  *   ib_create_ensemble: members are existing grids (the ensemble does not own
  *     them) that all have the same dim, the same rotate_split and the same
@@ -244,6 +244,24 @@ int ib_sweep_config(ib_grid_t g, int axis, int cfg[4]);
  * are distorted.  Only before the first step.  Errors: IB_ERR_ARG (axis, or
  * id not a candidate for this grid), IB_ERR_STATE (grid already stepped). */
 int ib_fix_sweep_config(ib_grid_t g, int axis, int id);
+
+/* Marker re-sorting (no counterpart in the paper, whose Lagrangian data
+ * migrate between processors instead; Sec. 4.1).  Internally the markers are
+ * numbered in the Morton order of their positions, so that neighbouring
+ * threads of interpolation and spreading touch neighbouring grid nodes; the
+ * numbering is taken from the initial positions, and structures that travel
+ * (Sec. 6.3: ellipses carried through the periodic box) can be re-numbered by
+ * their current positions.  Results are unchanged up to the summation order
+ * of the spreading atomics, and ib_read_markers / ib_set_markers /
+ * ib_save_state / ib_adjoint_run keep using the caller's order.
+ *   ib_resort_markers: re-number now (host-side sort of the current
+ *     positions; synchronises the grid's stream).
+ *   ib_set_resort_interval: re-number before every step n with n % every == 0
+ *     (n > 0) inside ib_step (each time synchronising the stream); 0 (the
+ *     default) never.  Ensemble steps and ib_adjoint_run do not re-number.
+ * Errors: IB_ERR_ARG (null grid, every < 0), IB_ERR_CUDA. */
+int ib_resort_markers(ib_grid_t g);
+int ib_set_resort_interval(ib_grid_t g, int every);
 
 /* Run n_steps steps with every kernel launched on its own and timed by CUDA
  * events on the grid's stream; kernel_ms[i] receives the total milliseconds

@@ -29,7 +29,8 @@ EXPORTS = ("ib_create_grid", "ib_add_fiber", "ib_set_velocity", "ib_step", "ib_r
            "ib_cyclic_solve_lines", "ib_split_solve", "ib_split_solve_noalloc", "ib_profile_step",
            "ib_kernel_name", "ib_create_ensemble", "ib_ensemble_step", "ib_destroy_ensemble",
            "ib_sweep_config", "ib_fix_sweep_config", "ib_adjoint_run", "ib_selftest_wait_timeout",
-           "ib_state_size", "ib_save_state", "ib_load_state", "ib_measure_peak")
+           "ib_state_size", "ib_save_state", "ib_load_state", "ib_measure_peak", "ib_resort_markers",
+           "ib_set_resort_interval")
 IB_PEAK_FP64_FMA, IB_PEAK_FP32_FMA, IB_PEAK_L2_ATOMIC = 0, 1, 2
 
 
@@ -80,6 +81,8 @@ def lib():
         L.ib_ensemble_step.argtypes = [vp, C.c_int]
         L.ib_destroy_ensemble.argtypes = [vp]
         L.ib_measure_peak.argtypes = [C.c_int, vp, dp]
+        L.ib_resort_markers.argtypes = [vp]
+        L.ib_set_resort_interval.argtypes = [vp, C.c_int]
         L.ib_sweep_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.ib_fix_sweep_config.argtypes = [vp, C.c_int, C.c_int]
         L.ib_adjoint_run.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp]
@@ -216,6 +219,14 @@ def ib_diagnostics(g, check=True):
     if check:
         _check(rc, "ib_diagnostics")
     return {k: getattr(d, k) for k, _ in ib_diag._fields_}, rc
+
+
+def ib_resort_markers(g):
+    _check(lib().ib_resort_markers(g), "ib_resort_markers")
+
+
+def ib_set_resort_interval(g, every):
+    _check(lib().ib_set_resort_interval(g, int(every)), "ib_set_resort_interval")
 
 
 def ib_measure_peak(kind, stream="current"):
@@ -392,6 +403,13 @@ class Grid:
     def adjoint(self, n_steps, X_target, checkpoint_every=20):
         """Advance n_steps; return (sum |X - X_target|^2, d loss / d kappa per connection)."""
         return ib_adjoint_run(self.h, n_steps, checkpoint_every, X_target, self.n_edges)
+
+    def resort_markers(self):
+        """Re-number the markers internally by their current positions."""
+        ib_resort_markers(self.h)
+
+    def set_resort_interval(self, every):
+        ib_set_resort_interval(self.h, every)
 
     def save_state(self):
         return ib_save_state(self.h)

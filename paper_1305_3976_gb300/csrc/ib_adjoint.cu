@@ -169,8 +169,18 @@ __global__ void k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, co
 }
 
 // A6: ub += (dN/du)^T V with N the skew-symmetric advection of the forward
-// step: for component c and axis a the term 1/2 (Ap up - Am um) / h_a, Ap, Am
-// linear in u; its partial derivatives are scattered with atomics.
+// step.  For component c and axis a the forward term at face x is
+//   1/2 (A+(x) u_c(x+a) - A-(x) u_c(x-a)) / h_a,
+// a == c: A+ = (u_c(x) + u_c(x+a))/2, A- = (u_c(x-a) + u_c(x))/2;
+// a != c: A+ = (u_a(x+a) + u_a(x+a-c))/2, A- = (u_a(x) + u_a(x-c))/2.
+// With S_ca(x) = V_c(x) / (2 h_a) its transpose scatters, per source x,
+//   a == c: S (u_c(x+a) - u_c(x-a))/2 to u_c(x), S (u_c(x+a)/2 + A+) to
+//           u_c(x+a), -S (u_c(x-a)/2 + A-) to u_c(x-a);
+//   a != c: S u_c(x+a)/2 to u_a(x+a) and u_a(x+a-c), S A+ to u_c(x+a),
+//           -S u_c(x-a)/2 to u_a(x) and u_a(x-c), -S A- to u_c(x-a).
+// The kernel gathers instead: the thread of face y of component b sums every
+// term whose target is (b, y), reading V and u around y, and adds the sum to
+// ub_b(y) once (no atomics, a fixed summation order).
 template <typename T, int DIM>
 __global__ void k_adj_adv(T *ub0, T *ub1, T *ub2, const T *u0, const T *u1, const T *u2, const T *v0, const T *v1,
                           const T *v2, int nx, int ny, int nz, T ihx, T ihy, T ihz) {
@@ -178,70 +188,169 @@ __global__ void k_adj_adv(T *ub0, T *ub1, T *ub2, const T *u0, const T *u1, cons
   T *ub[3] = {ub0, ub1, ub2};
   const T *u[3] = {u0, u1, u2}, *vv[3] = {v0, v1, v2};
   const T ih[3] = {ihx, ihy, ihz};
+  const int n[3] = {nx, ny, nz};
   for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % nx);
-    const long long t = o / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
-    const long long dp[3] = {i + 1 == nx ? 1 - nx : 1, j + 1 == ny ? (long long)nx * (1 - ny) : nx,
-                             k + 1 == nz ? (long long)nx * ny * (1 - nz) : (long long)nx * ny};
-    const long long dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? (long long)nx * (ny - 1) : -(long long)nx,
-                             k == 0 ? (long long)nx * ny * (nz - 1) : -(long long)nx * ny};
+    const int c0[3] = {(int)(o % nx), (int)((o / nx) % ny), (int)(o / ((long long)nx * ny))};
+    // linear index of y + d (periodic)
+    auto at = [&](int d0, int d1, int d2) -> long long {
+      const int d[3] = {d0, d1, d2};
+      long long idx = 0, mul = 1;
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      const T v = vv[c][o];
-      if (v == T(0)) continue;
-      const T *uc = u[c];
+      for (int a = 0; a < 3; ++a) {
+        if (a >= DIM) break;
+        int q = c0[a] + d[a];
+        q = q < 0 ? q + n[a] : (q >= n[a] ? q - n[a] : q);
+        idx += mul * q;
+        mul *= n[a];
+      }
+      return idx;
+    };
+    // unit vector along axis a times s
+    auto e3 = [](int a, int s, int (&d)[3]) {
+      d[0] = a == 0 ? s : 0;
+      d[1] = a == 1 ? s : 0;
+      d[2] = a == 2 ? s : 0;
+    };
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      const T *vb = vv[b], *ubv = u[b];
+      T acc = T(0);
+      int db[3];
+      // a == c == b: sources y, y - b, y + b
+      {
+        e3(b, 1, db);
+        const long long yp = at(db[0], db[1], db[2]), ym = at(-db[0], -db[1], -db[2]);
+        const T uy = ubv[o], up = ubv[yp], um = ubv[ym];
+        const T sy = T(0.5) * ih[b] * vb[o], sm = T(0.5) * ih[b] * vb[ym], sp = T(0.5) * ih[b] * vb[yp];
+        acc += sy * (T(0.5) * up - T(0.5) * um);
+        acc += sm * (T(0.5) * uy + T(0.5) * (um + uy));
+        acc -= sp * (T(0.5) * uy + T(0.5) * (uy + up));
+      }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        const T s = T(0.5) * ih[a] * v;  // d/d(product) of 1/2 (Ap up - Am um)/h
-        const T up = uc[o + dp[a]], um = uc[o + dm[a]];
-        if (a == c) {
-          const T u00 = uc[o];
-          const T Ap = T(0.5) * (u00 + up), Am = T(0.5) * (um + u00);
-          atomicAdd(ub[c] + o, s * (T(0.5) * up - T(0.5) * um));
-          atomicAdd(ub[c] + o + dp[a], s * (T(0.5) * up + Ap));
-          atomicAdd(ub[c] + o + dm[a], s * (-T(0.5) * um - Am));
-        } else {
-          const T *ua = u[a];
-          const long long i1 = o + dp[a], i2 = o + dp[a] + dm[c], i3 = o, i4 = o + dm[c];
-          const T Ap = T(0.5) * (ua[i1] + ua[i2]), Am = T(0.5) * (ua[i3] + ua[i4]);
-          atomicAdd(ub[a] + i1, s * T(0.5) * up);
-          atomicAdd(ub[a] + i2, s * T(0.5) * up);
-          atomicAdd(ub[c] + o + dp[a], s * Ap);
-          atomicAdd(ub[a] + i3, -s * T(0.5) * um);
-          atomicAdd(ub[a] + i4, -s * T(0.5) * um);
-          atomicAdd(ub[c] + o + dm[a], -s * Am);
-        }
+        if (a == b) continue;
+        int da[3];
+        e3(a, 1, da);
+        // c = b, axis a: S_ba A+ from source y - a, -S_ba A- from source y + a
+        const long long ya_m = at(-da[0], -da[1], -da[2]), ya_p = at(da[0], da[1], da[2]);
+        const T *ua = u[a];
+        const T Ap = T(0.5) * (ua[o] + ua[at(-db[0], -db[1], -db[2])]);
+        const T Am = T(0.5) * (ua[ya_p] + ua[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])]);
+        acc += T(0.5) * ih[a] * vb[ya_m] * Ap;
+        acc -= T(0.5) * ih[a] * vb[ya_p] * Am;
+        // c = a != b, axis b: the terms of component a's advection along b
+        // whose targets are u_b: S_ab u_a / 2 from sources y - b and
+        // y - b + a, -S_ab u_a / 2 from sources y and y + a
+        const T *va = vv[a];
+        const T shb = T(0.5) * ih[b];
+        acc += shb * va[at(-db[0], -db[1], -db[2])] * T(0.5) * ua[o];
+        acc += shb * va[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])] * T(0.5) * ua[ya_p];
+        acc -= shb * va[o] * T(0.5) * ua[at(-db[0], -db[1], -db[2])];
+        acc -= shb * va[ya_p] * T(0.5) * ua[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])];
       }
+      ub[b][o] += acc;
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// markers (one thread per (marker, component) or per marker; small counts)
+// markers.  The FP64 position arithmetic of a stencil (first node, weights
+// and their derivatives) runs once per (marker, component) pair in
+// k_adj_stencil, one pair per thread (GB300's FP64 pipe issues a warp
+// instruction at the same cost for 1 or 32 lanes); the node work then runs in
+// groups of ROWS lanes per pair (16 in 3D, 4 in 2D), lane r owning the stencil
+// row (y, z) = (r & 3, r >> 2), with shuffle reductions over the group.
+
+// stencil of every pair at the positions X (set 0: X^n, set 1: X^{n+1/2})
+template <typename T, int DIM>
+__global__ void k_adj_stencil(AdjMarkers<T> am, int set) {
+  const long long np = am.nm * DIM;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const long long k = p / DIM;
+  const int c = (int)(p % DIM);
+  int b[3];
+  T w[3][4], dw[3][4];
+  stencil_at<T, DIM>(set ? (const double *const *)am.Xh : am.X, k, c, am.inv_h, am.kernel, b, w, dw);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    am.stb[set][a * np + p] = b[a];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      am.stw[set][(4 * a + j) * np + p] = w[a][j];
+      am.stdw[set][(4 * a + j) * np + p] = dw[a][j];
+    }
+  }
+}
+
+// the lane's pair, its stencil row and the row's 4 node offsets
+template <typename T, int DIM>
+struct AdjRow {
+  static constexpr int ROWS = DIM == 3 ? 16 : 4;
+  long long p, k;
+  int c, jy, kz;
+  bool valid;
+  T wx[4], dwx[4], wy, dwy, wz, dwz;
+  long long node[4];
+  __device__ __forceinline__ AdjRow(const AdjMarkers<T> &am, int set) {
+    const long long np = am.nm * DIM;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    p = t / ROWS;
+    const int r = (int)(t % ROWS);
+    jy = r & 3;
+    kz = DIM == 3 ? r >> 2 : 0;
+    valid = p < np;
+    k = valid ? p / DIM : 0;
+    c = valid ? (int)(p % DIM) : 0;
+    wy = dwy = dwz = T(0);
+    wz = T(1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wx[j] = dwx[j] = T(0);
+      node[j] = 0;
+    }
+    if (!valid) return;
+    const int32_t *sb = am.stb[set];
+    const T *sw = am.stw[set], *sdw = am.stdw[set];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wx[j] = sw[j * np + p];
+      dwx[j] = sdw[j * np + p];
+    }
+    wy = sw[(4 + jy) * np + p];
+    dwy = sdw[(4 + jy) * np + p];
+    if (DIM == 3) {
+      wz = sw[(8 + kz) * np + p];
+      dwz = sdw[(8 + kz) * np + p];
+    }
+    const int bx = sb[p];
+    const long long row = (long long)am.n[0] * (wrapi(sb[np + p] + jy, am.n[1]) +
+                                                (DIM == 3 ? (long long)am.n[1] * wrapi(sb[2 * np + p] + kz, am.n[2]) : 0));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) node[j] = row + wrapi(bx + j, am.n[0]);
+  }
+};
+
+template <int ROWS, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int off = ROWS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
 
 // 1a: U_c = J(X^n) u_c
 template <typename T, int DIM>
 __global__ void k_adj_interp_fwd(AdjMarkers<T> am, const T *u0, const T *u1, const T *u2) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= am.nm * DIM) return;
-  const long long k = t / DIM;
-  const int c = (int)(t % DIM);
-  const T *uc = c == 0 ? u0 : (c == 1 ? u1 : u2);
-  int b[3];
-  T w[3][4], dw[3][4];
-  stencil_at<T, DIM>(am.X, k, c, am.inv_h, am.kernel, b, w, dw);
+  AdjRow<T, DIM> L(am, 0);
   T s = T(0);
-  for (int kz = 0; kz < (DIM == 3 ? 4 : 1); ++kz)
-    for (int jy = 0; jy < 4; ++jy)
-      for (int ix = 0; ix < 4; ++ix) {
-        const long long node = wrapi(b[0] + ix, am.n[0]) +
-                               (long long)am.n[0] * (wrapi(b[1] + jy, am.n[1]) +
-                                                     (DIM == 3 ? (long long)am.n[1] * wrapi(b[2] + kz, am.n[2]) : 0));
-        const T wz = DIM == 3 ? w[2][kz] : T(1);
-        s += uc[node] * (w[0][ix] * w[1][jy] * wz);
-      }
-  am.U[c][k] = s;
+  if (L.valid) {
+    const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += uc[L.node[j]] * L.wx[j];
+    s *= L.wy * L.wz;
+  }
+  s = group_sum<AdjRow<T, DIM>::ROWS>(s);
+  if (L.valid && L.jy == 0 && L.kz == 0) am.U[L.c][L.k] = s;
 }
 
 // 1b-1c: X^{n+1/2} = X + dt V / 2
@@ -261,66 +370,80 @@ __global__ void k_adj_half(AdjMarkers<T> am) {
 // derivative of the weights: Xhb_a += G_c sum_nodes fb_c dW/dX_a / h^d
 template <typename T, int DIM>
 __global__ void k_adj_spread_bar(AdjMarkers<T> am, const T *rb0, const T *rb1, const T *rb2, T dt_rho) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= am.nm * DIM) return;
-  const long long k = t / DIM;
-  const int c = (int)(t % DIM);
-  const T *rc = c == 0 ? rb0 : (c == 1 ? rb1 : rb2);
-  int b[3];
-  T w[3][4], dw[3][4];
-  stencil_at<T, DIM>(am.Xh, k, c, am.inv_h, am.kernel, b, w, dw);
+  AdjRow<T, DIM> L(am, 1);
   T s = T(0), sd[3] = {T(0), T(0), T(0)};
-  for (int kz = 0; kz < (DIM == 3 ? 4 : 1); ++kz)
-    for (int jy = 0; jy < 4; ++jy)
-      for (int ix = 0; ix < 4; ++ix) {
-        const long long node = wrapi(b[0] + ix, am.n[0]) +
-                               (long long)am.n[0] * (wrapi(b[1] + jy, am.n[1]) +
-                                                     (DIM == 3 ? (long long)am.n[1] * wrapi(b[2] + kz, am.n[2]) : 0));
-        const T r = rc[node];
-        const T wz = DIM == 3 ? w[2][kz] : T(1), dwz = DIM == 3 ? dw[2][kz] : T(0);
-        s += r * (w[0][ix] * w[1][jy] * wz);
-        sd[0] += r * (dw[0][ix] * w[1][jy] * wz);
-        sd[1] += r * (w[0][ix] * dw[1][jy] * wz);
-        if (DIM == 3) sd[2] += r * (w[0][ix] * w[1][jy] * dwz);
-      }
-  const T scale = dt_rho * (T)am.inv_vol;
-  am.Gb[c][k] = s * scale;
-  const T g = am.G[c][k] * scale;
+  if (L.valid) {
+    const T *rc = L.c == 0 ? rb0 : (L.c == 1 ? rb1 : rb2);
+    T r4[4];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) atomicAdd(am.Xhb[a] + k, (double)(g * sd[a]));
+    for (int j = 0; j < 4; ++j) r4[j] = rc[L.node[j]];
+    T sx = T(0), sdx = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      sx += r4[j] * L.wx[j];
+      sdx += r4[j] * L.dwx[j];
+    }
+    s = sx * L.wy * L.wz;
+    sd[0] = sdx * L.wy * L.wz;
+    sd[1] = sx * L.dwy * L.wz;
+    if (DIM == 3) sd[2] = sx * L.wy * L.dwz;
+  }
+  s = group_sum<AdjRow<T, DIM>::ROWS>(s);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) sd[a] = group_sum<AdjRow<T, DIM>::ROWS>(sd[a]);
+  if (L.valid && L.jy == 0 && L.kz == 0) {
+    const T scale = dt_rho * (T)am.inv_vol;
+    am.Gb[L.c][L.k] = s * scale;
+    const T g = am.G[L.c][L.k] * scale;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) atomicAdd(am.Xhb[a] + L.k, (double)(g * sd[a]));
+  }
 }
 
 // 2a adjoint (zero rest length): Xhb_a += sum_b kappa (Gb_b - Gb_a);
 // d(loss)/d kappa_e += (Xh_b - Xh_a).(Gb_a - Gb_b), counted once per
-// connection (from its CSR entry with a < b)
+// connection (from its CSR entry with a < b).  8 lanes per marker share its
+// CSR row (lane j takes entries j, j + 8, ...) and reduce with shuffles.
 template <typename T, int DIM>
 __global__ void k_adj_force_bar(AdjMarkers<T> am) {
-  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= am.nm) return;
-  double xa[DIM], acc[DIM];
-  T ga[DIM];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long a = t >> 3;
+  const int lane8 = (int)(t & 7);
+  const bool valid = a < am.nm;
+  double acc[DIM];
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) {
-    xa[q] = am.Xh[q][a];
-    ga[q] = am.Gb[q][a];
-    acc[q] = 0.0;
-  }
-  for (long long e = am.row[a]; e < am.row[a + 1]; ++e) {
-    const int b = am.col[e];
-    const double kap = am.kap[e];
-    double dot = 0.0;
+  for (int q = 0; q < DIM; ++q) acc[q] = 0.0;
+  if (valid) {
+    double xa[DIM];
+    T ga[DIM];
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
-      const double gb = (double)am.Gb[q][b];
-      acc[q] += kap * (gb - (double)ga[q]);
-      double d = am.Xh[q][b] - xa[q];
-      d -= am.H * rint(d / am.H);
-      dot += d * ((double)ga[q] - gb);
+      xa[q] = am.Xh[q][a];
+      ga[q] = am.Gb[q][a];
     }
-    if (b > a) am.dk[am.cedge[e]] += dot;
+    for (long long e = am.row[a] + lane8; e < am.row[a + 1]; e += 8) {
+      const int b = am.col[e];
+      const double kap = am.kap[e];
+      double dot = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        const double gb = (double)am.Gb[q][b];
+        acc[q] += kap * (gb - (double)ga[q]);
+        double d = am.Xh[q][b] - xa[q];
+        d -= am.H * rint(d / am.H);
+        dot += d * ((double)ga[q] - gb);
+      }
+      if (b > a) am.dk[am.cedge[e]] += dot;
+    }
   }
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) am.Xhb[q][a] += acc[q];
+  for (int q = 0; q < DIM; ++q)
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+  if (valid && lane8 == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) am.Xhb[q][a] += acc[q];
+  }
 }
 
 // 1b-1c adjoint: Xb <- Xb + Xhb; vbar = dt Xb' + dt/2 Xhb;
@@ -342,32 +465,31 @@ __global__ void k_adj_update_bar(AdjMarkers<T> am) {
 // 1a adjoint: ub_c += Ub_c W (spreading without 1/h^d); Xb_a += Ub_c sum u_c dW/dX_a
 template <typename T, int DIM>
 __global__ void k_adj_interp_bar(AdjMarkers<T> am, const T *u0, const T *u1, const T *u2, T *ub0, T *ub1, T *ub2) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= am.nm * DIM) return;
-  const long long k = t / DIM;
-  const int c = (int)(t % DIM);
-  const T *uc = c == 0 ? u0 : (c == 1 ? u1 : u2);
-  T *ubc = c == 0 ? ub0 : (c == 1 ? ub1 : ub2);
-  int b[3];
-  T w[3][4], dw[3][4];
-  stencil_at<T, DIM>(am.X, k, c, am.inv_h, am.kernel, b, w, dw);
-  const T Ub = am.Ub[c][k];
+  AdjRow<T, DIM> L(am, 0);
   T sd[3] = {T(0), T(0), T(0)};
-  for (int kz = 0; kz < (DIM == 3 ? 4 : 1); ++kz)
-    for (int jy = 0; jy < 4; ++jy)
-      for (int ix = 0; ix < 4; ++ix) {
-        const long long node = wrapi(b[0] + ix, am.n[0]) +
-                               (long long)am.n[0] * (wrapi(b[1] + jy, am.n[1]) +
-                                                     (DIM == 3 ? (long long)am.n[1] * wrapi(b[2] + kz, am.n[2]) : 0));
-        const T wz = DIM == 3 ? w[2][kz] : T(1), dwz = DIM == 3 ? dw[2][kz] : T(0);
-        atomicAdd(ubc + node, Ub * (w[0][ix] * w[1][jy] * wz));
-        const T un = uc[node];
-        sd[0] += un * (dw[0][ix] * w[1][jy] * wz);
-        sd[1] += un * (w[0][ix] * dw[1][jy] * wz);
-        if (DIM == 3) sd[2] += un * (w[0][ix] * w[1][jy] * dwz);
-      }
+  T Ub = T(0);
+  if (L.valid) {
+    const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
+    T *ubc = L.c == 0 ? ub0 : (L.c == 1 ? ub1 : ub2);
+    Ub = am.Ub[L.c][L.k];
+    const T wr = L.wy * L.wz;
+    T sx = T(0), sdx = T(0);
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) atomicAdd(am.Xb[a] + k, (double)(Ub * sd[a]));
+    for (int j = 0; j < 4; ++j) {
+      atomicAdd(ubc + L.node[j], Ub * (L.wx[j] * wr));
+      const T un = uc[L.node[j]];
+      sx += un * L.wx[j];
+      sdx += un * L.dwx[j];
+    }
+    sd[0] = sdx * wr;
+    sd[1] = sx * L.dwy * L.wz;
+    if (DIM == 3) sd[2] = sx * L.wy * L.dwz;
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) sd[a] = group_sum<AdjRow<T, DIM>::ROWS>(sd[a]);
+  if (L.valid && L.jy == 0 && L.kz == 0)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) atomicAdd(am.Xb[a] + L.k, (double)(Ub * sd[a]));
 }
 
 // --------------------------------------------------------------------------
@@ -420,11 +542,14 @@ template <typename T>
 cudaError_t adjoint_markers_pre(const AdjMarkers<T> &am, const T *const u[3], cudaStream_t s) {
   if (am.nm == 0) return cudaSuccess;
   const unsigned g = (unsigned)((am.nm * am.dim + 255) / 256);
+  const unsigned gr = (unsigned)((am.nm * am.dim * (am.dim == 3 ? 16 : 4) + 255) / 256);
   if (am.dim == 2) {
-    k_adj_interp_fwd<T, 2><<<g, 256, 0, s>>>(am, u[0], u[1], u[1]);
+    k_adj_stencil<T, 2><<<g, 256, 0, s>>>(am, 0);
+    k_adj_interp_fwd<T, 2><<<gr, 256, 0, s>>>(am, u[0], u[1], u[1]);
     k_adj_half<T, 2><<<g, 256, 0, s>>>(am);
   } else {
-    k_adj_interp_fwd<T, 3><<<g, 256, 0, s>>>(am, u[0], u[1], u[2]);
+    k_adj_stencil<T, 3><<<g, 256, 0, s>>>(am, 0);
+    k_adj_interp_fwd<T, 3><<<gr, 256, 0, s>>>(am, u[0], u[1], u[2]);
     k_adj_half<T, 3><<<g, 256, 0, s>>>(am);
   }
   return cudaGetLastError();
@@ -434,17 +559,20 @@ template <typename T>
 cudaError_t adjoint_markers_post(const AdjMarkers<T> &am, const T *const rb[3], T dt_rho, const T *const u[3],
                                  T *const ub[3], cudaStream_t s) {
   if (am.nm == 0) return cudaSuccess;
-  const unsigned g = (unsigned)((am.nm * am.dim + 255) / 256), g1 = (unsigned)((am.nm + 255) / 256);
+  const unsigned g = (unsigned)((am.nm * am.dim + 255) / 256), g8 = (unsigned)((am.nm * 8 + 255) / 256);
+  const unsigned gr = (unsigned)((am.nm * am.dim * (am.dim == 3 ? 16 : 4) + 255) / 256);
   if (am.dim == 2) {
-    k_adj_spread_bar<T, 2><<<g, 256, 0, s>>>(am, rb[0], rb[1], rb[1], dt_rho);
-    k_adj_force_bar<T, 2><<<g1, 256, 0, s>>>(am);
+    k_adj_stencil<T, 2><<<g, 256, 0, s>>>(am, 1);
+    k_adj_spread_bar<T, 2><<<gr, 256, 0, s>>>(am, rb[0], rb[1], rb[1], dt_rho);
+    k_adj_force_bar<T, 2><<<g8, 256, 0, s>>>(am);
     k_adj_update_bar<T, 2><<<g, 256, 0, s>>>(am);
-    k_adj_interp_bar<T, 2><<<g, 256, 0, s>>>(am, u[0], u[1], u[1], ub[0], ub[1], ub[1]);
+    k_adj_interp_bar<T, 2><<<gr, 256, 0, s>>>(am, u[0], u[1], u[1], ub[0], ub[1], ub[1]);
   } else {
-    k_adj_spread_bar<T, 3><<<g, 256, 0, s>>>(am, rb[0], rb[1], rb[2], dt_rho);
-    k_adj_force_bar<T, 3><<<g1, 256, 0, s>>>(am);
+    k_adj_stencil<T, 3><<<g, 256, 0, s>>>(am, 1);
+    k_adj_spread_bar<T, 3><<<gr, 256, 0, s>>>(am, rb[0], rb[1], rb[2], dt_rho);
+    k_adj_force_bar<T, 3><<<g8, 256, 0, s>>>(am);
     k_adj_update_bar<T, 3><<<g, 256, 0, s>>>(am);
-    k_adj_interp_bar<T, 3><<<g, 256, 0, s>>>(am, u[0], u[1], u[2], ub[0], ub[1], ub[2]);
+    k_adj_interp_bar<T, 3><<<gr, 256, 0, s>>>(am, u[0], u[1], u[2], ub[0], ub[1], ub[2]);
   }
   return cudaGetLastError();
 }

@@ -305,6 +305,11 @@ struct AdjMarkers {
   const double *kap;
   const int32_t *cedge;  // connection index of every CSR entry
   double *dk;            // d(loss)/d kappa, per connection
+  // stencils of X^n (set 0) and X^{n+1/2} (set 1) for every (marker,
+  // component) pair p = k d + c: first node per axis stb[a np + p], node
+  // weights stw[(4 a + j) np + p] and their derivatives stdw (same layout)
+  int32_t *stb[2];
+  T *stw[2], *stdw[2];
   int64_t nm;
   double dt, H;
   double inv_h[3];

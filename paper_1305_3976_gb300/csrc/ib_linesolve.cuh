@@ -496,7 +496,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs<T> &a, const Blk &B
     sweep_x_line<T, R, PRO, EPI, FULL, EXT>(a, xc, F, Fin, comp, line, lane);
 }
 template <typename T, int R, int PRO, int EPI, bool FULL, bool EXT>
-__global__ void __launch_bounds__(256) k_sweep_x(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, PRO == PRO_DIV && R == 4 ? 3 : 1) k_sweep_x(const SweepArgs<T> a) {
   pdl_wait();
   pdl_release();
   sweep_x_body<T, R, PRO, EPI, FULL, EXT>(a, hw_blk());

@@ -196,6 +196,7 @@ struct ib_grid_s {
   int tune[3] = {-1, -1, -1};   // sweep configuration per axis (autotuned)
   int tune_r[3] = {-1, -1, -1}; // the best one for the sweeps with a prologue or epilogue (no TMA kernel)
   bool fixed[3] = {false, false, false};  // set by ib_fix_sweep_config: not timed
+  int resort_every = 0;         // ib_set_resort_interval: re-sort the markers every that many steps
   cudaStream_t s = nullptr;     // library stream
   cudaStream_t user = nullptr;  // caller stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -418,27 +419,32 @@ uint64_t morton_key(const unsigned q[3], int d) {
   return key;
 }
 
-int upload_markers(ib_grid_s *g) {
-  if (g->markers_uploaded) return IB_OK;
-  const int d = g->dim;
-  const int64_t nm = g->nm, ne = g->ne, nt = g->nt;
-  // Internal marker order: Morton order of the initial positions (wrapped into
-  // the box), so that runs of consecutive markers are spatially compact.
-  // perm[k] = caller's index of internal marker k; inv is its inverse.
+// Morton order of nm positions (component a of marker k at X[k * sk + a * sa])
+// wrapped into the box: order[i] = index of the i-th marker in that order
+void morton_order(const double *X, int64_t nm, int d, double H, int64_t sk, int64_t sa, std::vector<int32_t> &order) {
   std::vector<uint64_t> key(nm);
   for (int64_t k = 0; k < nm; ++k) {
     unsigned q[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) {
-      double x = g->hX[k * d + a] / g->desc.H;
+      double x = X[k * sk + a * sa] / H;
       x -= floor(x);
       int c = (int)(x * 1024.0);
       q[a] = (unsigned)(c < 0 ? 0 : (c > 1023 ? 1023 : c));
     }
     key[k] = morton_key(q, d);
   }
-  std::vector<int32_t> perm(nm), inv(nm);
-  for (int64_t k = 0; k < nm; ++k) perm[k] = (int32_t)k;
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+  order.resize(nm);
+  for (int64_t k = 0; k < nm; ++k) order[k] = (int32_t)k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+}
+
+// The structure arrays of the internal marker numbering perm (perm[k] =
+// caller's index of internal marker k): connections as CSR by marker (both
+// directions) and as an edge list, triangles, and perm itself, written into
+// the grid's existing device buffers.
+int upload_structure(ib_grid_s *g, const std::vector<int32_t> &perm) {
+  const int64_t nm = g->nm, ne = g->ne, nt = g->nt;
+  std::vector<int32_t> inv(nm);
   for (int64_t k = 0; k < nm; ++k) inv[perm[k]] = (int32_t)k;
   std::vector<int32_t> E(2 * ne), Tr(3 * nt);
   for (int64_t e = 0; e < 2 * ne; ++e) E[e] = inv[g->hE[e]];
@@ -462,6 +468,40 @@ int upload_markers(ib_grid_s *g) {
     kap[pa] = kap[pb] = g->hK[e];
     rest[pa] = rest[pb] = g->hR[e];
   }
+  IB_CUDA(cudaMemcpyAsync(g->row, row.data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, g->s));
+  if (ne) {
+    IB_CUDA(cudaMemcpyAsync(g->col, col.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->cedge, cedge.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    if (g->esz == 4) {
+      for (int64_t e = 0; e < 2 * ne; ++e) {
+        kapf[e] = (float)kap[e];
+        restf[e] = (float)rest[e];
+      }
+      IB_CUDA(cudaMemcpyAsync(g->kapT, kapf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+      IB_CUDA(cudaMemcpyAsync(g->restT, restf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    } else {
+      IB_CUDA(cudaMemcpyAsync(g->kapT, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+      IB_CUDA(cudaMemcpyAsync(g->restT, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+    }
+    IB_CUDA(cudaMemcpyAsync(g->edges, E.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
+  }
+  if (nt) IB_CUDA(cudaMemcpyAsync(g->tris, Tr.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, g->s));
+  if (nm) IB_CUDA(cudaMemcpyAsync(g->perm, perm.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));  // host vectors above go out of scope
+  return IB_OK;
+}
+
+int upload_markers(ib_grid_s *g) {
+  if (g->markers_uploaded) return IB_OK;
+  const int d = g->dim;
+  const int64_t nm = g->nm, ne = g->ne, nt = g->nt;
+  // Internal marker order: Morton order of the initial positions (wrapped into
+  // the box), so that runs of consecutive markers are spatially compact.
+  // perm[k] = caller's index of internal marker k.
+  std::vector<int32_t> perm;
+  morton_order(g->hX.data(), nm, d, g->desc.H, d, 1, perm);
   std::vector<double> soa(nm * d);
   for (int64_t k = 0; k < nm; ++k)
     for (int a = 0; a < d; ++a) soa[a * nm + k] = g->hX[(int64_t)perm[k] * d + a];
@@ -528,30 +568,12 @@ int upload_markers(ib_grid_s *g) {
   g->cedge = (int32_t *)(base + o_cedge);
   IB_CUDA(cudaMemsetAsync(g->mk, 0, off, g->s));
   if (nm) IB_CUDA(cudaMemcpyAsync(g->X[0], soa.data(), sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
-  IB_CUDA(cudaMemcpyAsync(g->row, row.data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, g->s));
   if (ne) {
-    IB_CUDA(cudaMemcpyAsync(g->col, col.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    IB_CUDA(cudaMemcpyAsync(g->cedge, cedge.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    IB_CUDA(cudaMemcpyAsync(g->kap, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    IB_CUDA(cudaMemcpyAsync(g->rest, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    if (es == 4) {
-      for (int64_t e = 0; e < 2 * ne; ++e) {
-        kapf[e] = (float)kap[e];
-        restf[e] = (float)rest[e];
-      }
-      IB_CUDA(cudaMemcpyAsync(g->kapT, kapf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-      IB_CUDA(cudaMemcpyAsync(g->restT, restf.data(), sizeof(float) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    } else {
-      IB_CUDA(cudaMemcpyAsync(g->kapT, kap.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-      IB_CUDA(cudaMemcpyAsync(g->restT, rest.data(), sizeof(double) * 2 * ne, cudaMemcpyHostToDevice, g->s));
-    }
-    IB_CUDA(cudaMemcpyAsync(g->edges, E.data(), sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->ekap, g->hK.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
     IB_CUDA(cudaMemcpyAsync(g->erest, g->hR.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, g->s));
   }
-  if (nt) IB_CUDA(cudaMemcpyAsync(g->tris, Tr.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, g->s));
-  if (nm) IB_CUDA(cudaMemcpyAsync(g->perm, perm.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, g->s));
-  IB_CUDA(cudaStreamSynchronize(g->s));  // host vectors above go out of scope
+  int rc = upload_structure(g, perm);  // synchronises the stream (soa goes out of scope)
+  if (rc) return rc;
   g->markers_uploaded = true;
   return IB_OK;
 }
@@ -667,6 +689,40 @@ int prepare(ib_grid_s *g) {
   return IB_OK;
 }
 
+// Re-number the markers internally in the Morton order of their current
+// positions: X^n and U^{n-1} are permuted, the connection CSR, edge list,
+// triangles and the caller permutation rebuilt, and the grid locations of X^n
+// recomputed; every other marker array is rewritten by the next step before
+// it is read.  Pointers do not change, so captured graphs stay valid.
+// Synchronises the grid's stream.
+int resort_markers(ib_grid_s *g) {
+  if (!g->markers_uploaded || g->nm == 0) return IB_OK;
+  const int d = g->dim;
+  const int64_t nm = g->nm;
+  const size_t es = g->esz;
+  std::vector<double> X(nm * d), X2(nm * d);
+  std::vector<char> Uo(es * nm * d), Uo2(es * nm * d);
+  std::vector<int32_t> perm(nm), perm2(nm), ord;
+  IB_CUDA(cudaMemcpyAsync(X.data(), g->X[0], sizeof(double) * nm * d, cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaMemcpyAsync(Uo.data(), g->Uold[0], es * nm * d, cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaMemcpyAsync(perm.data(), g->perm, sizeof(int32_t) * nm, cudaMemcpyDeviceToHost, g->s));
+  IB_CUDA(cudaStreamSynchronize(g->s));
+  morton_order(X.data(), nm, d, g->desc.H, 1, nm, ord);
+  for (int64_t k = 0; k < nm; ++k) {
+    perm2[k] = perm[ord[k]];
+    for (int a = 0; a < d; ++a) {
+      X2[a * nm + k] = X[a * nm + ord[k]];
+      memcpy(Uo2.data() + es * (a * nm + k), Uo.data() + es * (a * nm + ord[k]), es);
+    }
+  }
+  IB_CUDA(cudaMemcpyAsync(g->X[0], X2.data(), sizeof(double) * nm * d, cudaMemcpyHostToDevice, g->s));
+  IB_CUDA(cudaMemcpyAsync(g->Uold[0], Uo2.data(), es * nm * d, cudaMemcpyHostToDevice, g->s));
+  int rc = upload_structure(g, perm2);  // synchronises the stream
+  if (rc) return rc;
+  g->loc_valid = false;
+  return ensure_loc(g);
+}
+
 // ---------------------------------------------------------------------------
 // Discrete adjoint driver (kernels in ib_adjoint.cu).
 
@@ -751,7 +807,12 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
   char *adjf = pool.get(z.fbytes * (4 * d + 4));
   const size_t mbytes = pad256(sizeof(double) * d * (nm + 1)), tbytes = pad256(sizeof(T) * d * (nm + 1));
   char *adjm = pool.get(2 * mbytes + 3 * tbytes + pad256(sizeof(double) * (ne + 1)));
-  if (!cks || !tape || !adjf || !adjm)
+  // stencil scratch of the marker adjoint: 2 sets of 3 first nodes and 12
+  // weights and derivatives per (marker, component)
+  const int64_t npair = nm * d + 1;
+  const size_t sbytes = pad256(sizeof(int32_t) * 3 * npair), swbytes = pad256(sizeof(T) * 12 * npair);
+  char *adjs = pool.get(2 * (sbytes + 2 * swbytes));
+  if (!cks || !tape || !adjf || !adjm || !adjs)
     return fail(IB_ERR_OOM, "adjoint: %zu bytes of checkpoints and tape do not fit",
                 ck_bytes * (nseg + 1) + tape_bytes * ck);
   // forward with checkpoints
@@ -851,6 +912,12 @@ int adjoint_t(ib_grid_s *g, int n_steps, int ck, const double *X_target, double 
   for (int a = 0; a < d; ++a) am.inv_vol /= g->h[a];
   am.dim = d;
   am.kernel = D.kernel;
+  for (int st = 0; st < 2; ++st) {
+    char *b = adjs + st * (sbytes + 2 * swbytes);
+    am.stb[st] = (int32_t *)b;
+    am.stw[st] = (T *)(b + sbytes);
+    am.stdw[st] = (T *)(b + sbytes + swbytes);
+  }
   SweepArgs<T> sa;
   memset(&sa, 0, sizeof(sa));
   for (int a = 0; a < 3; ++a) {
@@ -1114,6 +1181,7 @@ int ib_step(ib_grid_t g, int n_steps) {
   if (rc) return rc;
   if ((rc = prepare(g))) return rc;
   for (int i = 0; i < n_steps; ++i) {
+    if (g->resort_every > 0 && g->step > 0 && g->step % g->resort_every == 0 && (rc = resort_markers(g))) return rc;
     if (g->step == 0) {
       if ((rc = enqueue_step(g, true, 0, nullptr))) return rc;
     } else {
@@ -1194,6 +1262,21 @@ int ib_fix_sweep_config(ib_grid_t g, int axis, int id) {
   g->tune[axis] = id;
   g->tune_r[axis] = id == kTmaCfg ? -1 : id;
   g->fixed[axis] = true;
+  return IB_OK;
+}
+
+int ib_resort_markers(ib_grid_t g) {
+  if (!g) return fail(IB_ERR_ARG, "null grid");
+  int rc = enter(g);
+  if (!rc) rc = upload_markers(g);
+  if (!rc) rc = resort_markers(g);
+  if (rc) return rc;
+  return leave(g);
+}
+
+int ib_set_resort_interval(ib_grid_t g, int every) {
+  if (!g || every < 0) return fail(IB_ERR_ARG, "bad argument");
+  g->resort_every = every;
   return IB_OK;
 }
 
@@ -1515,6 +1598,8 @@ int ib_adjoint_run(ib_grid_t g, int n_steps, int checkpoint_every, const double 
 // walks the class's member table (launch_batch); the classes run side by
 // side on their own streams, and in each class the marker chain runs beside
 // the right-hand side as in a single grid's step.
+constexpr size_t kEnsembleGroup = 4;  // members per group of a size class (one batched launch)
+
 struct ib_ensemble_s {
   std::vector<ib_grid_s *> m;
   cudaStream_t s = nullptr, user = nullptr;
@@ -1660,16 +1745,26 @@ int ib_create_ensemble(const ib_grid_t *members, int n_members, void *stream, ib
       ib_destroy_ensemble(e);
       return fail(IB_ERR_CUDA, "ensemble event creation failed");
     }
-  // size classes in order of first appearance
+  // size classes in order of first appearance, each split into groups of at
+  // most kEnsembleGroup members (groups run on their own streams, so the
+  // marker stages of some overlap the field stages of others)
+  std::vector<std::vector<int>> cls;
   for (int i = 0; i < n_members; ++i) {
     const ib_grid_s *g = members[i];
     size_t c = 0;
-    for (; c < e->cls.size(); ++c) {
-      const ib_grid_s *h = members[e->cls[c][0]];
+    for (; c < cls.size(); ++c) {
+      const ib_grid_s *h = members[cls[c][0]];
       if (h->prec == g->prec && h->n[0] == g->n[0] && h->n[1] == g->n[1] && h->n[2] == g->n[2]) break;
     }
-    if (c == e->cls.size()) e->cls.emplace_back();
-    e->cls[c].push_back(i);
+    if (c == cls.size()) cls.emplace_back();
+    cls[c].push_back(i);
+  }
+  for (const std::vector<int> &c : cls) {
+    const size_t ng = (c.size() + kEnsembleGroup - 1) / kEnsembleGroup;
+    for (size_t q = 0; q < ng; ++q) {
+      e->cls.emplace_back();
+      for (size_t i = q; i < c.size(); i += ng) e->cls.back().push_back(c[i]);
+    }
   }
   const size_t nc = e->cls.size();
   e->cs.assign(nc, nullptr);

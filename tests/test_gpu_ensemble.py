@@ -61,9 +61,9 @@ def test_ensemble_member_matches_oracle():
 
 
 def test_ensemble_more_members_than_one_launch_holds_and_mixed_precision():
-    # 26 members of one size (two batched launches per kernel: 24 + 2), two
-    # FP64 members of another size in their own class, and one member without
-    # markers
+    # 26 members of one size (seven groups of at most 4, each a batched
+    # launch per kernel), two FP64 members of another size in their own
+    # class, and one member without markers
     many = I.ensemble_members(count=26, sizes=(16,), seed=3)
     grids = [_grid(sc, "fp32") for sc in many]
     solo = [_grid(sc, "fp32") for sc in many]
