@@ -1809,6 +1809,12 @@ int ib_ensemble_step(ib_ensemble_t e, int n_steps) {
     IB_CUDA(cudaEventRecord(e->ev_join[i], e->m[i]->s));
     IB_CUDA(cudaStreamWaitEvent(e->s, e->ev_join[i], 0));
   }
+  // capture every phase's graph up front, so that no capture happens between steps
+  const int phases = e->m[0]->desc.rotate_split ? e->dim : 1;
+  for (int ph = 0; ph < phases; ++ph) {
+    int rc = ens_graph(e, ph);
+    if (rc) return rc;
+  }
   for (int i = 0; i < n_steps; ++i) {
     const int64_t step = e->m[0]->step;
     if (step == 0) {
@@ -1816,8 +1822,6 @@ int ib_ensemble_step(ib_ensemble_t e, int n_steps) {
       if (rc) return rc;
     } else {
       const int phase = e->m[0]->desc.rotate_split ? (int)(step % e->dim) : 0;
-      int rc = ens_graph(e, phase);
-      if (rc) return rc;
       IB_CUDA(cudaGraphLaunch(e->graph[phase], e->s));
     }
     for (ib_grid_s *g : e->m) g->step++;
