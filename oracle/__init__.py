@@ -233,6 +233,8 @@ class Simulation:
         d = P.dim
         shp = field_shape(P)
         self.u = np.zeros((d,) + shp) if u0 is None else _f64(u0).copy()
+        if self.u.shape != (d,) + shp:
+            raise ValueError(f"u0 has shape {self.u.shape}, the grid needs {(d,) + shp}")
         self.p = np.zeros(shp)
         self.psi = np.zeros(shp)
         self.Nprev = np.zeros((d,) + shp)
@@ -243,6 +245,10 @@ class Simulation:
         ne = self.edges.shape[0]
         self.kappa = _f64(np.zeros(ne) if kappa is None else kappa).copy()
         self.rest = _f64(np.zeros(ne) if rest is None else rest).copy()
+        if ne and (self.edges.shape[1] != 2 or self.kappa.shape != (ne,) or self.rest.shape != (ne,)):
+            raise ValueError("edges must be (n_e, 2) with n_e stiffnesses and rest lengths")
+        if ne and (self.edges.min() < 0 or self.edges.max() >= self.X.shape[0]):
+            raise ValueError("edge index out of range")
         self.n = 0
 
     def _state(self):

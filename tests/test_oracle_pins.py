@@ -508,3 +508,16 @@ def test_energy_decays_and_its_window_increases_vanish_with_dt():
     assert all(0.06 < d < 0.10 for d in decay), decay
     assert abs(decay[2] - decay[1]) < abs(decay[1] - decay[0]), decay
     assert inc[0] / inc[1] > 2.0 and inc[1] / inc[2] > 2.0, inc
+
+
+def test_simulation_rejects_misshapen_inputs():
+    # the binding hands raw pointers to C: a wrong shape must raise, not corrupt memory
+    P = O.params(2, (16, 16), rho=1.0, mu=0.1, dt=1e-3)
+    X = I.ellipse_points(8, 0.2, 0.25)
+    E, K, R = I.closed_fiber_connections(8, 1.0)
+    with pytest.raises(ValueError):
+        O.Simulation(P, X, E, K, R, u0=np.zeros((8, 3)))
+    with pytest.raises(ValueError):
+        O.Simulation(P, X, E, K[:-1], R)
+    with pytest.raises(ValueError):
+        O.Simulation(P, X[:4], E, K, R)
