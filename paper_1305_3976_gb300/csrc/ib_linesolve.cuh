@@ -48,6 +48,11 @@ __device__ __forceinline__ void ld4_ro(const double *p, double (&v)[4]) {
 
 __device__ __forceinline__ int next_wrap(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 
+// dynamic shared memory of the strided sweeps: D.u^{n+1} of every element of
+// the CTA between the divergence prologue and the update of p after the solve
+// (sweep_s_div_smem bytes; none for the other sweeps)
+extern __shared__ __align__(16) unsigned char ibg_sweep_dyn[];
+
 // D.u at cell (i, j, k): sum_a (u_a at face i_a + 1 - u_a at face i_a) / h_a
 // (loads only)
 template <typename T>
@@ -563,51 +568,91 @@ __device__ __forceinline__ void sweep_s_body(const SweepArgs<T> &a, const int ax
         if (xok && (FULL || e < len)) ldv<VW>(tgt + o0 + e * stride, old[EARLY ? e : 0]);
     }
   } else {
-    // Step 3e right-hand side -rho/dt D.u^{n+1}; the new D.u and p are stored
-    // after every load of the chunk
+    // Step 3e right-hand side -rho/dt D.u^{n+1}, accumulated in v axis by
+    // axis in the order of div_at (x, y, z) from loads alone, so that the
+    // loads of a phase are all independent and none waits behind a store;
+    // D.u^{n+1} itself is parked in shared memory for the update of p and D.u
+    // after the solve (sweep_s_div_tail)
     const int nz = a.dim == 3 ? a.n[2] : 1;
-    const int jo = axis == 1 ? -1 : other, ko = axis == 1 ? other : -1;  // fixed coordinate
-    const int xe = x0 + VW == nx ? -x0 : VW;   // offset of the face after the last column
+    // x part: the face after a lane's last column is the next lane's first
+    // column; the last lane of the CTA, and the lane that ends the row (which
+    // wraps to column 0), load it
+    {
+      const int xe = x0 + VW == nx ? -x0 : VW;
+      const bool xload = lane == 31 || x0 + VW == nx;
 #pragma unroll
-    // read-only loads (every element is read before this thread alone writes
-    // it) and the new D.u and p stored at once, so that only the right-hand
-    // sides stay live
-    for (int e = 0; e < CH; ++e) {
-#pragma unroll
-      for (int c = 0; c < VW; ++c) v[e][c] = T(0);
-      if (xok && (FULL || e < len)) {
-        const int t = start + e;
-        const int j = axis == 1 ? t : jo, k = axis == 1 ? ko : t;
+      for (int e = 0; e < CH; ++e) {
+        const bool ok = xok && (FULL || e < len);
         const int o = o0 + e * stride;
-        const int dy = j + 1 == ny ? nx * (1 - ny) : nx;
-        T u0[VW], v0[VW], v1[VW], dv[VW], pv[VW];
-        ldv_ro<VW>(a.u[0] + o, u0);
-        const T ue = ld_ro(a.u[0] + o + xe);
-        ldv_ro<VW>(a.u[1] + o, v0);
-        ldv_ro<VW>(a.u[1] + o + dy, v1);
-        ldv_ro<VW>(a.div + o, dv);
-        ldv_ro<VW>(a.p + o, pv);
-        T w0[VW], w1[VW];
-        if (a.dim == 3) {
-          const int dz = k + 1 == nz ? nx * ny * (1 - nz) : nx * ny;
-          ldv_ro<VW>(a.u[2] + o, w0);
-          ldv_ro<VW>(a.u[2] + o + dz, w1);
-        }
-        T dn[VW], pn[VW];
+        T u0[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) u0[c] = T(0);
+        if (ok) ldv_ro<VW>(a.u[0] + o, u0);
+        const T nb = __shfl_down_sync(IBG_FULL, u0[0], 1);
+        const T ue = ok && xload ? ld_ro(a.u[0] + o + xe) : nb;
 #pragma unroll
         for (int c = 0; c < VW; ++c) {
           const T up = c + 1 < VW ? u0[c + 1 < VW ? c + 1 : 0] : ue;
-          T d = (up - u0[c]) * a.inv_h[0];
-          d += (v1[c] - v0[c]) * a.inv_h[1];
-          if (a.dim == 3) d += (w1[c] - w0[c]) * a.inv_h[2];
-          dn[c] = d;
-          pn[c] = kept_p(a, pv[c]) - a.chi_mu_half * (d + dv[c]);
-          v[e][c] = a.pro_scale * d;
+          v[e][c] = ok ? (up - u0[c]) * a.inv_h[0] : T(0);
         }
-        stv<VW>(a.div + o, dn);
-        stv<VW>(a.p + o, pn);
       }
     }
+    // the component along the line (v on y lines, w on z lines): its
+    // neighbour is the chunk's next element, after the chunk the next chunk's
+    // first element (element 0 at the end of the line)
+    auto along = [&](const T *f, T ih) {
+      const bool any = xok && (FULL || len > 0);
+      const int tn = start + len < nl ? start + len : 0;
+      T cur[VW], nxt[VW];
+#pragma unroll
+      for (int c = 0; c < VW; ++c) cur[c] = nxt[c] = T(0);
+      if (any) {
+        ldv_ro<VW>(f + o0, cur);
+        ldv_ro<VW>(f + base + tn * stride, nxt);
+      }
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        const bool ok = xok && (FULL || e < len);
+        T nb[VW];
+#pragma unroll
+        for (int c = 0; c < VW; ++c) nb[c] = nxt[c];
+        if (e + 1 < CH && (FULL || e + 1 < len) && xok) ldv_ro<VW>(f + o0 + (e + 1) * stride, nb);
+        if (ok) {
+#pragma unroll
+          for (int c = 0; c < VW; ++c) v[e][c] += (nb[c] - cur[c]) * ih;
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) cur[c] = nb[c];
+      }
+    };
+    // a component across the lines: its neighbour lies `off` elements away
+    // (the line's fixed coordinate + 1, periodic)
+    auto across = [&](const T *f, int off, T ih) {
+#pragma unroll
+      for (int e = 0; e < CH; ++e)
+        if (xok && (FULL || e < len)) {
+          const int o = o0 + e * stride;
+          T f0[VW], f1[VW];
+          ldv_ro<VW>(f + o, f0);
+          ldv_ro<VW>(f + o + off, f1);
+#pragma unroll
+          for (int c = 0; c < VW; ++c) v[e][c] += (f1[c] - f0[c]) * ih;
+        }
+    };
+    if (axis == 1) along(a.u[1], a.inv_h[1]);
+    else across(a.u[1], other + 1 == ny ? nx * (1 - ny) : nx, a.inv_h[1]);
+    if (a.dim == 3) {
+      if (axis == 2) along(a.u[2], a.inv_h[2]);
+      else across(a.u[2], other + 1 == nz ? nx * ny * (1 - nz) : nx * ny, a.inv_h[2]);
+    }
+    T *sd = reinterpret_cast<T *>(ibg_sweep_dyn);
+#pragma unroll
+    for (int e = 0; e < CH; ++e)
+#pragma unroll
+      for (int c = 0; c < VW; ++c) {
+        sd[(e * VW + c) * (32 * W) + threadIdx.x] = v[e][c];
+        v[e][c] = a.pro_scale * v[e][c];
+      }
   }
   __syncthreads();  // lp
   const T gCH = lp[CH];
@@ -729,6 +774,36 @@ __device__ __forceinline__ void sweep_s_body(const SweepArgs<T> &a, const int ax
 #pragma unroll
     for (int e = 0; e < CH; ++e)
       if (FULL || e < len) stv<VW>(F + o0 + e * stride, v[e]);
+    if (PRO == PRO_DIV) {
+      // sweep_s_div_tail: Step 3f without psi, p <- p_keep p - chi mu / 2
+      // (D.u^{n+1} + D.u^n), and D.u^n <- D.u^{n+1} (parked in shared memory
+      // by the prologue), G elements per batch of loads
+      const T *sd = reinterpret_cast<const T *>(ibg_sweep_dyn);
+      constexpr int G = 16 / VW < CH ? 16 / VW : CH;
+#pragma unroll
+      for (int e0 = 0; e0 < CH; e0 += G) {
+        T dv[G][VW], pv[G][VW];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (FULL || e0 + g < len) {
+            ldv_ro<VW>(a.div + o0 + (e0 + g) * stride, dv[g]);
+            ldv_ro<VW>(a.p + o0 + (e0 + g) * stride, pv[g]);
+          }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (FULL || e0 + g < len) {
+            T dn[VW], pn[VW];
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+              const T d = sd[((e0 + g) * VW + c) * (32 * W) + threadIdx.x];
+              dn[c] = d;
+              pn[c] = kept_p(a, pv[g][c]) - a.chi_mu_half * (d + dv[g][c]);
+            }
+            stv<VW>(a.div + o0 + (e0 + g) * stride, dn);
+            stv<VW>(a.p + o0 + (e0 + g) * stride, pn);
+          }
+      }
+    }
   } else {
     // psi stores first, then every load of the old values, then the sums:
     // no load waits behind a store
@@ -798,25 +873,31 @@ __host__ __device__ constexpr int xcap(int i) { return i == 0 ? 2 : i == 1 ? 4 :
 // Whether strided configuration i can run this sweep: it must cover the line
 // with less than twice its length (n <= CH W < 2n; the smallest shape,
 // CH = 8 and W = 8, covers every shorter line), n_x must be a multiple of VW,
-// and VW CH is at most 32 values per thread in FP32, 16 for the divergence
-// prologue and in FP64 (32 in FP64 with VW = 1 and W = 16).
-inline bool strided_cfg_ok(int i, int nl, int nx, bool dbl, bool div) {
+// and VW CH is at most 32 values per thread (FP64: VW = 1 only).
+inline bool strided_cfg_ok(int i, int nl, int nx, bool dbl) {
   const StridedCfg c = strided_cfg(i);
   const bool smallest = c.ch == 8 && c.w == 8;
   if (c.ch * c.w < nl || (!smallest && c.ch * c.w >= 2 * nl) || nx % c.vw) return false;
   if (dbl) return c.vw == 1;
-  return c.vw * c.ch <= (div ? 16 : 32);
+  return c.vw * c.ch <= 32;
+}
+
+// dynamic shared memory of a strided sweep with the divergence prologue: one
+// value per element of the CTA's lines
+inline size_t sweep_s_div_smem(int cfg, size_t elem) {
+  const StridedCfg c = strided_cfg(cfg);
+  return (size_t)c.ch * c.vw * 32 * c.w * elem;
 }
 
 // The default choice (no autotuning): the first valid configuration in the
 // order of preference below.
-inline int strided_cfg_default(int nl, int nx, bool dbl, bool div) {
+inline int strided_cfg_default(int nl, int nx, bool dbl) {
   static const int pref_f[] = {3, 0, 6, 1, 4, 7, 9, 2, 5, 8, 10};
   static const int pref_d[] = {0, 3, 6, 10, 8};
   const int *pref = dbl ? pref_d : pref_f;
   const int np = dbl ? 5 : 11;
   for (int k = 0; k < np; ++k)
-    if (strided_cfg_ok(pref[k], nl, nx, dbl, div)) return pref[k];
+    if (strided_cfg_ok(pref[k], nl, nx, dbl)) return pref[k];
   return -1;
 }
 
@@ -839,24 +920,25 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
   } else {
     const int other = axis == 1 ? (a.dim == 3 ? a.n[2] : 1) : a.n[1];
     const int nx = a.n[0];
-    const bool dbl = sizeof(T) == 8, div = PRO == PRO_DIV;
-    if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl, div))
-      cfg = strided_cfg_default(nl, nx, dbl, div);
+    const bool dbl = sizeof(T) == 8;
+    if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl)) cfg = strided_cfg_default(nl, nx, dbl);
     auto grid = [&](int v) { return dim3((unsigned)((nx / v + 31) / 32), other, nfields); };
-#define IBG_S(I)                                                                                        \
-  case I: {                                                                                             \
-    constexpr StridedCfg c = strided_cfg(I);                                                            \
-    if (nl == c.ch * c.w)                                                                               \
-      return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
-    return launch_pdl(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, grid(c.vw), dim3(32 * c.w), 0, s, a, axis); \
+    const size_t smem = PRO == PRO_DIV ? sweep_s_div_smem(cfg, sizeof(T)) : 0;
+    auto run = [&](auto kernel, int vw, int w) -> cudaError_t {
+      if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      return launch_pdl(kernel, grid(vw), dim3(32 * w), smem, s, a, axis);
+    };
+#define IBG_S(I)                                                                 \
+  case I: {                                                                      \
+    constexpr StridedCfg c = strided_cfg(I);                                     \
+    if (nl == c.ch * c.w) return run(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, c.vw, c.w); \
+    return run(k_sweep_s<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, c.vw, c.w);  \
   }
     if constexpr (sizeof(T) == 8) {
       switch (cfg) { IBG_S(0) IBG_S(3) IBG_S(6) IBG_S(8) IBG_S(10) default: return cudaErrorInvalidValue; }
-    } else if constexpr (PRO == PRO_DIV) {
-      switch (cfg) {
-        IBG_S(0) IBG_S(1) IBG_S(3) IBG_S(4) IBG_S(6) IBG_S(8) IBG_S(10)
-        default: return cudaErrorInvalidValue;
-      }
     } else {
       switch (cfg) {
         IBG_S(0) IBG_S(1) IBG_S(2) IBG_S(3) IBG_S(4) IBG_S(5) IBG_S(6) IBG_S(7) IBG_S(8) IBG_S(9) IBG_S(10)
@@ -890,26 +972,28 @@ cudaError_t launch_sweep_batch_t(int axis, int nfields, const SweepArgs<T> *a, i
   }
   const int other = axis == 1 ? (a0.dim == 3 ? a0.n[2] : 1) : a0.n[1];
   const int nx = a0.n[0];
-  const bool dbl = sizeof(T) == 8, div = PRO == PRO_DIV;
-  if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl, div)) cfg = strided_cfg_default(nl, nx, dbl, div);
+  const bool dbl = sizeof(T) == 8;
+  if (cfg < 0 || cfg >= kStridedCfgs || !strided_cfg_ok(cfg, nl, nx, dbl)) cfg = strided_cfg_default(nl, nx, dbl);
   auto grids = [&](int v) {
     for (int i = 0; i < n; ++i) g[i] = dim3((unsigned)((nx / v + 31) / 32), other, nfields);
     return g.data();
   };
-#define IBG_SB(I)                                                                                           \
-  case I: {                                                                                                 \
-    constexpr StridedCfg c = strided_cfg(I);                                                                \
-    if (nl == c.ch * c.w)                                                                                   \
-      return launch_batch(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, a, grids(c.vw), n, dim3(32 * c.w), s, axis); \
-    return launch_batch(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, a, grids(c.vw), n, dim3(32 * c.w), s, axis); \
+  const size_t smem = PRO == PRO_DIV ? sweep_s_div_smem(cfg, sizeof(T)) : 0;
+  auto run = [&](auto kernel, int vw, int w) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_batch_smem(kernel, a, grids(vw), n, dim3(32 * w), smem, s, axis);
+  };
+#define IBG_SB(I)                                                                  \
+  case I: {                                                                        \
+    constexpr StridedCfg c = strided_cfg(I);                                       \
+    if (nl == c.ch * c.w) return run(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, true, EXT>, c.vw, c.w); \
+    return run(k_sweep_s_b<T, c.vw, c.ch, c.w, PRO, EPI, false, EXT>, c.vw, c.w);  \
   }
   if constexpr (sizeof(T) == 8) {
     switch (cfg) { IBG_SB(0) IBG_SB(3) IBG_SB(6) IBG_SB(8) IBG_SB(10) default: return cudaErrorInvalidValue; }
-  } else if constexpr (PRO == PRO_DIV) {
-    switch (cfg) {
-      IBG_SB(0) IBG_SB(1) IBG_SB(3) IBG_SB(4) IBG_SB(6) IBG_SB(8) IBG_SB(10)
-      default: return cudaErrorInvalidValue;
-    }
   } else {
     switch (cfg) {
       IBG_SB(0) IBG_SB(1) IBG_SB(2) IBG_SB(3) IBG_SB(4) IBG_SB(5) IBG_SB(6) IBG_SB(7) IBG_SB(8) IBG_SB(9) IBG_SB(10)

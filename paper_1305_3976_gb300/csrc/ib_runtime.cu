@@ -195,6 +195,8 @@ struct ib_grid_s {
   bool tuned = false;
   int tune[3] = {-1, -1, -1};   // sweep configuration per axis (autotuned)
   int tune_r[3] = {-1, -1, -1}; // the best one for the sweeps with a prologue or epilogue (no TMA kernel)
+  int tune_psi[3] = {-1, -1, -1};  // plain psi sweeps (one field, the psi operator)
+  int tune_div[3] = {-1, -1, -1};  // the first psi sweep (divergence prologue; no TMA kernel)
   bool fixed[3] = {false, false, false};  // set by ib_fix_sweep_config: not timed
   int resort_every = 0;         // ib_set_resort_interval: re-sort the markers every that many steps
   cudaStream_t s = nullptr;     // library stream
@@ -337,8 +339,8 @@ void plan_step(ib_grid_s *g, bool first, int phase, StepPlan<T> &P) {
     P.pro[k] = pro;
     P.epi[k] = epi;
     P.nf[k] = 1;
-    P.cfg[k] = plain ? g->tune[ax] : g->tune_r[ax];
-    P.cfg_r[k] = g->tune_r[ax];
+    P.cfg[k] = pro == PRO_DIV ? g->tune_div[ax] : plain ? g->tune_psi[ax] : g->tune_r[ax];
+    P.cfg_r[k] = pro == PRO_DIV ? g->tune_div[ax] : g->tune_r[ax];
   }
   P.nsw = k;
 }
@@ -614,10 +616,14 @@ int ensure_loc(ib_grid_s *g) {
   return IB_OK;
 }
 
-// Autotuner: for every axis, time each candidate sweep configuration on the
-// d scratch fields (zero before the first step) with the plain load/store sweep,
-// 1 + 3 launches each, and keep the fastest; the step's sweeps along that
-// axis then use it.
+// Autotuner: for every axis, time each candidate sweep configuration in the
+// roles the step uses it in, 1 + 3 launches each, and keep the fastest per
+// role: the plain momentum sweep on the d scratch fields (tune; tune_r, the
+// best register kernel, also serves the sweeps with an epilogue and the
+// ensembles' batched sweeps), the plain psi sweep on one scratch field with
+// the psi operator (tune_psi), and the first psi sweep with its divergence
+// prologue (tune_div), which reads the state's velocity and writes D.u and p
+// into two temporary fields.
 template <typename T>
 int autotune_t(ib_grid_s *g) {
   const int d = g->dim;
@@ -629,42 +635,71 @@ int autotune_t(ib_grid_s *g) {
     sa.inv_h[a] = (T)(1.0 / g->h[a]);
   }
   sa.dim = d;
-  cudaEvent_t e0, e1;
-  IB_CUDA(cudaEventCreate(&e0));
-  IB_CUDA(cudaEventCreate(&e1));
+  const size_t fb = ((size_t)g->cells * g->esz + 255) / 256 * 256;
+  char *tmp = nullptr;
+  if (cudaMalloc(&tmp, 2 * fb) != cudaSuccess) return fail(IB_ERR_OOM, "autotune scratch of %zu bytes", 2 * fb);
+  SweepArgs<T> sd = sa;
+  for (int a = 0; a < 3; ++a) sd.u[a] = (const T *)g->u[a < d ? a : 0];
+  sd.f[0] = (T *)g->scr[0];
+  sd.div = (T *)tmp;
+  sd.p = (T *)(tmp + fb);
+  sd.pro_scale = T(1);
+  sd.p_keep = T(1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = IB_OK;
+  if (cudaMemsetAsync(tmp, 0, 2 * fb, g->s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = fail(IB_ERR_CUDA, "autotune setup");
+  // ms of 3 launches after one untimed launch, or < 0 on failure
+  auto time = [&](int ax, int pro, int nf, const SweepArgs<T> &a, int cfg) -> float {
+    if (launch_sweep<T>(ax, pro, EPI_STORE, nf, a, g->s, cfg) != cudaSuccess) return -1.f;
+    cudaEventRecord(e0, g->s);
+    for (int r = 0; r < 3; ++r) launch_sweep<T>(ax, pro, EPI_STORE, nf, a, g->s, cfg);
+    cudaEventRecord(e1, g->s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
   for (int ax = 0; ax < d && !rc; ++ax) {
     if (g->fixed[ax]) continue;
     sa.co = coef_of<T>(g->coef[0][ax]);
+    SweepArgs<T> sp = sa;
+    sp.co = coef_of<T>(g->coef[1][ax]);
+    sd.co = sp.co;
     int cand[16];
     const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 16);
-    float best = 1e30f, best_r = 1e30f;
+    float best = 1e30f, best_r = 1e30f, best_p = 1e30f, best_d = 1e30f;
     for (int i = 0; i < nc && !rc; ++i) {
-      if (launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, cand[i]) != cudaSuccess) {
+      const float ms = time(ax, PRO_LOAD, d, sa, cand[i]);
+      const float mp = ms < 0.f ? ms : time(ax, PRO_LOAD, 1, sp, cand[i]);
+      const float md = mp < 0.f || cand[i] == kTmaCfg ? mp : time(ax, PRO_DIV, 1, sd, cand[i]);
+      if (ms < 0.f || mp < 0.f || md < 0.f) {
         rc = fail(IB_ERR_CUDA, "autotune launch");
         break;
       }
-      cudaEventRecord(e0, g->s);
-      for (int r = 0; r < 3; ++r) launch_sweep<T>(ax, PRO_LOAD, EPI_STORE, d, sa, g->s, cand[i]);
-      cudaEventRecord(e1, g->s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = fail(IB_ERR_CUDA, "autotune sync");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best) {
         best = ms;
         g->tune[ax] = cand[i];
+      }
+      if (mp < best_p) {
+        best_p = mp;
+        g->tune_psi[ax] = cand[i];
       }
       if (cand[i] != kTmaCfg && ms < best_r) {
         best_r = ms;
         g->tune_r[ax] = cand[i];
       }
+      if (cand[i] != kTmaCfg && md < best_d) {
+        best_d = md;
+        g->tune_div[ax] = cand[i];
+      }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(g->s);
+  cudaFree(tmp);
   return rc;
 }
 
@@ -1259,8 +1294,8 @@ int ib_fix_sweep_config(ib_grid_t g, int axis, int id) {
   bool ok = false;
   for (int i = 0; i < nc; ++i) ok = ok || cand[i] == id;
   if (!ok) return fail(IB_ERR_ARG, "configuration %d is not a candidate for axis %d of this grid", id, axis);
-  g->tune[axis] = id;
-  g->tune_r[axis] = id == kTmaCfg ? -1 : id;
+  g->tune[axis] = g->tune_psi[axis] = id;
+  g->tune_r[axis] = g->tune_div[axis] = id == kTmaCfg ? -1 : id;
   g->fixed[axis] = true;
   return IB_OK;
 }

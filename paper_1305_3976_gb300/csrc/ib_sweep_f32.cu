@@ -27,7 +27,7 @@ int sweep_candidates(int axis, int nl, int nx, bool dbl, int *out, int max) {
     for (int i = 0; i < kXCaps && k < max; ++i) out[k++] = i;
   } else {
     for (int i = 0; i < kStridedCfgs && k < max; ++i)
-      if (strided_cfg_ok(i, nl, nx, dbl, false)) out[k++] = i;
+      if (strided_cfg_ok(i, nl, nx, dbl)) out[k++] = i;
     if (!dbl && nx % 4 == 0 && (nl <= 256 || nl % 2 == 0) && k < max) out[k++] = kTmaCfg;
   }
   return k;
