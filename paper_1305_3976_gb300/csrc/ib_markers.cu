@@ -149,11 +149,10 @@ struct StencilLanes {
   bool valid;
   T wx[4], wrow;  // x weights; product of this row's y (and z) weights
   int bx, yrow, zrow;
-  __device__ __forceinline__ StencilLanes(const MarkerArgs &m, const int32_t *lb, const T *lw, const Blk &B) {
-    // 32-bit index arithmetic: marker count * d * ROWS < 2^31 (checked on the host)
-    const unsigned gt = B.x * blockDim.x + threadIdx.x;
-    const unsigned pair = gt / ROWS;
-    row = (int)(gt & (ROWS - 1));
+  // pair: the (marker, component) index k d + c; row: this lane's stencil row
+  __device__ __forceinline__ StencilLanes(const MarkerArgs &m, const int32_t *lb, const T *lw, unsigned pair,
+                                          int row_) {
+    row = row_;
     k = pair / DIM;
     c = (int)(pair - k * DIM);
     valid = k < (unsigned)m.nm;
@@ -192,9 +191,9 @@ struct StencilNodes3 {
   bool valid;
   T w0, w1;
   unsigned o0, o1;  // element offsets of the two nodes (fields hold < 2^31 elements)
-  __device__ __forceinline__ StencilNodes3(const MarkerArgs &m, const int32_t *lb, const T *lw, const Blk &B) {
-    // 32-bit unsigned thread index: at most 2^25 markers (checked on the host), 96 lanes each
-    const unsigned gw = (B.x * blockDim.x + threadIdx.x) >> 5;
+  StencilNodes3() = default;
+  // gw: the (marker, component) index k 3 + c
+  __device__ __forceinline__ StencilNodes3(const MarkerArgs &m, const int32_t *lb, const T *lw, unsigned gw) {
     const int lane = threadIdx.x & 31;
     k = gw / 3;
     c = (int)(gw - k * 3);
@@ -276,21 +275,49 @@ __device__ __forceinline__ void row4_add(double *r, int xs, int nx, const double
   for (int i = 0; i < 4; ++i) atomicAdd(r + (xs + i < nx ? xs + i : xs + i - nx), v[i]);
 }
 
+// (marker, component) pairs per lane group of k_interp and per warp of
+// k_spread3: their loads are issued together, so that a group waits for one
+// round of load latency per kInterpItems / kSpreadItems pairs.  Measured on
+// GB300 (1 / 2 / 4 pairs): spreading 26.6 / 24.6 / 24.6 us at 128^3 and
+// 287 / 251 / 236 us at 512^3 (8 x 64 002 markers); interpolation 20.7 / 21.1 /
+// 23.0 us at 128^3 and 185 / 181 / 178 us at 512^3, so it keeps one pair at
+// the size where it is on the step's critical path.
+constexpr int kInterpItems = 1;
+constexpr int kSpreadItems = 4;
+
 // Step 1a: U_c = sum over the 4^d nodes of u_c(node) prod_a phi_a, at X^n.
 template <typename T, int DIM>
 __device__ __forceinline__ void interp_body(const MarkerArgs &m, const T *const u0, const T *const u1,
                                             const T *const u2, const Blk &B) {
-  StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w, B);
-  T s = T(0);
-  if (L.valid) {
-    const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
-    T v[4];
-    row4(uc + L.row_offset(m), L.bx, m.n[0], v);
-    s = (v[0] * L.wx[0] + v[1] * L.wx[1] + v[2] * L.wx[2] + v[3] * L.wx[3]) * L.wrow;
+  constexpr int ROWS = StencilLanes<T, DIM>::ROWS;
+  // 32-bit index arithmetic: marker count * d * ROWS < 2^31 (checked on the host)
+  const unsigned gt = B.x * blockDim.x + threadIdx.x;
+  const unsigned grp = gt / ROWS;
+  const int row = (int)(gt & (ROWS - 1));
+  T s[kInterpItems];
+  bool ok[kInterpItems];
+  unsigned kk[kInterpItems];
+  int cc[kInterpItems];
+#pragma unroll
+  for (int i = 0; i < kInterpItems; ++i) {
+    StencilLanes<T, DIM> L(m, m.locI_b, (const T *)m.locI_w, grp * kInterpItems + i, row);
+    ok[i] = L.valid;
+    kk[i] = L.k;
+    cc[i] = L.c;
+    s[i] = T(0);
+    if (L.valid) {
+      const T *uc = L.c == 0 ? u0 : (L.c == 1 ? u1 : u2);
+      T v[4];
+      row4(uc + L.row_offset(m), L.bx, m.n[0], v);
+      s[i] = (v[0] * L.wx[0] + v[1] * L.wx[1] + v[2] * L.wx[2] + v[3] * L.wx[3]) * L.wrow;
+    }
   }
 #pragma unroll
-  for (int off = StencilLanes<T, DIM>::ROWS / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (L.valid && L.row == 0) ((T *)m.U[L.c])[L.k] = s;
+  for (int i = 0; i < kInterpItems; ++i) {
+#pragma unroll
+    for (int off = ROWS / 2; off > 0; off >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+    if (ok[i] && row == 0) ((T *)m.U[cc[i]])[kk[i]] = s[i];
+  }
 }
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_interp(const MarkerArgs m, const T *const u0, const T *const u1,
@@ -407,7 +434,9 @@ __global__ void __launch_bounds__(256) k_force_b(const __grid_constant__ Batch<M
 template <typename T, int DIM>
 __device__ __forceinline__ void spread_body(const MarkerArgs &m, T *const f0, T *const f1, T *const f2,
                                             const Blk &B) {
-  StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w, B);
+  constexpr int ROWS = StencilLanes<T, DIM>::ROWS;
+  const unsigned gt = B.x * blockDim.x + threadIdx.x;
+  StencilLanes<T, DIM> L(m, m.locS_b, (const T *)m.locS_w, gt / ROWS, (int)(gt & (ROWS - 1)));
   if (!L.valid) return;
   T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
   const T val = ((const T *)m.G[L.c])[L.k] * (T)m.spread_scale * L.wrow;
@@ -439,12 +468,22 @@ __global__ void __launch_bounds__(256) k_spread_b(const __grid_constant__ Batch<
 template <typename T>
 __device__ __forceinline__ void spread3_body(const MarkerArgs &m, T *const f0, T *const f1, T *const f2,
                                              const Blk &B) {
-  StencilNodes3<T> L(m, m.locS_b, (const T *)m.locS_w, B);
-  if (!L.valid) return;
-  T *fc = L.c == 0 ? f0 : (L.c == 1 ? f1 : f2);
-  const T g = ((const T *)m.G[L.c])[L.k] * (T)m.spread_scale;
-  atomicAdd(fc + L.o0, g * L.w0);
-  atomicAdd(fc + L.o1, g * L.w1);
+  // 32-bit unsigned warp index: at most 2^25 markers (checked on the host)
+  const unsigned gw = (B.x * blockDim.x + threadIdx.x) >> 5;
+  T gv[kSpreadItems];
+  StencilNodes3<T> L[kSpreadItems];
+#pragma unroll
+  for (int i = 0; i < kSpreadItems; ++i) {
+    L[i] = StencilNodes3<T>(m, m.locS_b, (const T *)m.locS_w, gw * kSpreadItems + i);
+    gv[i] = L[i].valid ? ((const T *)m.G[L[i].c])[L[i].k] * (T)m.spread_scale : T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < kSpreadItems; ++i)
+    if (L[i].valid) {
+      T *fc = L[i].c == 0 ? f0 : (L[i].c == 1 ? f1 : f2);
+      atomicAdd(fc + L[i].o0, gv[i] * L[i].w0);
+      atomicAdd(fc + L[i].o1, gv[i] * L[i].w1);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread3(const MarkerArgs m, T *const f0, T *const f1, T *const f2) {
@@ -494,7 +533,7 @@ cudaError_t launch_locate(const MarkerArgs &m, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
-  const unsigned g = nblocks(m.nm * m.dim * (m.dim == 3 ? 16 : 4), 256);
+  const unsigned g = nblocks((m.nm * m.dim + kInterpItems - 1) / kInterpItems * (m.dim == 3 ? 16 : 4), 256);
   if (m.dim == 2) return launch_pdl(k_interp<T, 2>, dim3(g), dim3(256), 0, s, m, u[0], u[1], u[1]);
   return launch_pdl(k_interp<T, 3>, dim3(g), dim3(256), 0, s, m, u[0], u[1], u[2]);
   return cudaGetLastError();
@@ -527,7 +566,8 @@ cudaError_t launch_spread(const MarkerArgs &m, T *const f[3], cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
   if (m.dim == 2)
     return launch_pdl(k_spread<T, 2>, dim3(nblocks(m.nm * 2 * 4, 256)), dim3(256), 0, s, m, f[0], f[1], f[1]);
-  return launch_pdl(k_spread3<T>, dim3(nblocks(m.nm * 3 * 32, 256)), dim3(256), 0, s, m, f[0], f[1], f[2]);
+  return launch_pdl(k_spread3<T>, dim3(nblocks((m.nm * 3 + kSpreadItems - 1) / kSpreadItems * 32, 256)), dim3(256), 0,
+                    s, m, f[0], f[1], f[2]);
   return cudaGetLastError();
 }
 
@@ -544,7 +584,8 @@ cudaError_t launch_interp_batch(const MarkerFieldArgs *a, int n, cudaStream_t s)
   if (n < 1) return cudaSuccess;
   const int d = a[0].m.dim;
   std::vector<dim3> g(n);
-  for (int i = 0; i < n; ++i) g[i] = dim3(a[i].m.nm ? nblocks(a[i].m.nm * d * (d == 3 ? 16 : 4), 256) : 0);
+  for (int i = 0; i < n; ++i)
+    g[i] = dim3(a[i].m.nm ? nblocks((a[i].m.nm * d + kInterpItems - 1) / kInterpItems * (d == 3 ? 16 : 4), 256) : 0);
   if (d == 2) return launch_batch(k_interp_b<T, 2>, a, g.data(), n, dim3(256), s);
   return launch_batch(k_interp_b<T, 3>, a, g.data(), n, dim3(256), s);
 }
@@ -578,7 +619,10 @@ cudaError_t launch_spread_batch(const MarkerFieldArgs *a, int n, cudaStream_t s)
   if (n < 1) return cudaSuccess;
   const int d = a[0].m.dim;
   std::vector<dim3> g(n);
-  for (int i = 0; i < n; ++i) g[i] = dim3(a[i].m.nm ? nblocks(a[i].m.nm * d * (d == 3 ? 32 : 4), 256) : 0);
+  for (int i = 0; i < n; ++i)
+    g[i] = dim3(a[i].m.nm ? (d == 3 ? nblocks((a[i].m.nm * 3 + kSpreadItems - 1) / kSpreadItems * 32, 256)
+                                    : nblocks(a[i].m.nm * 2 * 4, 256))
+                          : 0);
   if (d == 2) return launch_batch(k_spread_b<T, 2>, a, g.data(), n, dim3(256), s);
   return launch_batch(k_spread3_b<T>, a, g.data(), n, dim3(256), s);
 }
