@@ -9,7 +9,7 @@
 //          with A = prod (I - D_aa) symmetric, and D^T = -G;
 //   3c-3d  u' = u + M^{-1} R, M = prod (I - a D_aa) symmetric;
 //   3a-3b  R = dt [(mu L u - G p* + f)/rho - (c1 N(u) + c2 N(u^{n-1}))],
-//          N quadratic in u (its Jacobian-transpose is scattered with atomics);
+//          N quadratic in u (its Jacobian-transpose gathered per target face);
 //   2b     f = S(X^{n+1/2}) G (spreading; adjoint: interpolation, plus the
 //          derivative of the weights),
 //   2a     G = F(X^{n+1/2}; kappa), zero rest length: G_a = sum kappa (X_b - X_a),
