@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--sweep-config", default=None,
                     help="comma-separated line-solve configuration ids per axis (as printed under "
                          "sweep_configs) to use instead of autotuning, e.g. to profile a run's choice")
-    ap.add_argument("--profile-one-step", action="store_true",
-                    help="bracket the first per-kernel profiling step with cudaProfilerStart/Stop, so that a "
-                         "profiler started with --profile-from-start off captures exactly that step's kernels")
+    ap.add_argument("--profile-one-step", type=int, nargs="?", const=0, default=None, metavar="I",
+                    help="bracket per-kernel profiling step I (default 0; the steps rotate the split order) "
+                         "with cudaProfilerStart/Stop, so that a profiler started with --profile-from-start off "
+                         "captures exactly that step's kernels")
     return ap.parse_args()
 
 
@@ -415,7 +416,7 @@ def run_ours(args, rank, world, local):
     for i in range(nprof):
         flush.zero_()
         torch.cuda.synchronize()
-        bracket = args.profile_one_step and i == 0
+        bracket = args.profile_one_step is not None and i == args.profile_one_step
         if bracket:
             torch.cuda.profiler.start()
         for k, v in g.profile(1).items():
