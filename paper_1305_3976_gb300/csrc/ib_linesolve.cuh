@@ -864,9 +864,13 @@ __host__ __device__ constexpr StridedCfg strided_cfg(int i) {
        : i == 7 ? StridedCfg{2, 16, 16}
        : i == 8 ? StridedCfg{1, 16, 32}
        : i == 9 ? StridedCfg{2, 16, 32}
-                : StridedCfg{1, 32, 16};
+       : i == 10 ? StridedCfg{1, 32, 16}
+       // (id 11 is the TMA kernel, kTmaCfg)
+       : i == 12 ? StridedCfg{1, 32, 4}
+       : i == 13 ? StridedCfg{2, 16, 8}
+                 : StridedCfg{1, 32, 8};
 }
-constexpr int kStridedCfgs = 11;
+constexpr int kStridedCfgs = 15;  // ids 0 .. 14 except kTmaCfg
 constexpr int kXCaps = 4;
 __host__ __device__ constexpr int xcap(int i) { return i == 0 ? 2 : i == 1 ? 4 : i == 2 ? 8 : 1 << 20; }
 
@@ -875,10 +879,11 @@ __host__ __device__ constexpr int xcap(int i) { return i == 0 ? 2 : i == 1 ? 4 :
 // CH = 8 and W = 8, covers every shorter line), n_x must be a multiple of VW,
 // and VW CH is at most 32 values per thread (FP64: VW = 1 only).
 inline bool strided_cfg_ok(int i, int nl, int nx, bool dbl) {
+  if (i < 0 || i >= kStridedCfgs || i == kTmaCfg) return false;
   const StridedCfg c = strided_cfg(i);
   const bool smallest = c.ch == 8 && c.w == 8;
   if (c.ch * c.w < nl || (!smallest && c.ch * c.w >= 2 * nl) || nx % c.vw) return false;
-  if (dbl) return c.vw == 1;
+  if (dbl) return c.vw == 1 && i <= 10;  // the FP64 kernels are instantiated for ids 0, 3, 6, 8, 10
   return c.vw * c.ch <= 32;
 }
 
@@ -942,6 +947,7 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
     } else {
       switch (cfg) {
         IBG_S(0) IBG_S(1) IBG_S(2) IBG_S(3) IBG_S(4) IBG_S(5) IBG_S(6) IBG_S(7) IBG_S(8) IBG_S(9) IBG_S(10)
+        IBG_S(12) IBG_S(13) IBG_S(14)
         default: return cudaErrorInvalidValue;
       }
     }
@@ -997,6 +1003,7 @@ cudaError_t launch_sweep_batch_t(int axis, int nfields, const SweepArgs<T> *a, i
   } else {
     switch (cfg) {
       IBG_SB(0) IBG_SB(1) IBG_SB(2) IBG_SB(3) IBG_SB(4) IBG_SB(5) IBG_SB(6) IBG_SB(7) IBG_SB(8) IBG_SB(9) IBG_SB(10)
+      IBG_SB(12) IBG_SB(13) IBG_SB(14)
       default: return cudaErrorInvalidValue;
     }
   }

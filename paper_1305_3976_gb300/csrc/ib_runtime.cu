@@ -197,6 +197,8 @@ struct ib_grid_s {
   int tune_r[3] = {-1, -1, -1}; // the best one for the sweeps with a prologue or epilogue (no TMA kernel)
   int tune_psi[3] = {-1, -1, -1};  // plain psi sweeps (one field, the psi operator)
   int tune_div[3] = {-1, -1, -1};  // the first psi sweep (divergence prologue; no TMA kernel)
+  int tune_addu[3] = {-1, -1, -1}; // the last momentum sweep (u^n + e epilogue; no TMA kernel)
+  int tune_p[3] = {-1, -1, -1};    // the last psi sweep (p + psi epilogue; no TMA kernel)
   bool fixed[3] = {false, false, false};  // set by ib_fix_sweep_config: not timed
   int resort_every = 0;         // ib_set_resort_interval: re-sort the markers every that many steps
   cudaStream_t s = nullptr;     // library stream
@@ -322,8 +324,8 @@ void plan_step(ib_grid_s *g, bool first, int phase, StepPlan<T> &P) {
     P.pro[k] = PRO_LOAD;
     P.epi[k] = last ? EPI_ADDU : EPI_STORE;
     P.nf[k] = d;
-    P.cfg[k] = last ? g->tune_r[ax] : g->tune[ax];
-    P.cfg_r[k] = g->tune_r[ax];
+    P.cfg[k] = last ? g->tune_addu[ax] : g->tune[ax];
+    P.cfg_r[k] = last ? g->tune_addu[ax] : g->tune_r[ax];
   }
   // Step 3e (psi, one sweep per axis) with Step 3f folded into the first and
   // last sweeps
@@ -339,8 +341,8 @@ void plan_step(ib_grid_s *g, bool first, int phase, StepPlan<T> &P) {
     P.pro[k] = pro;
     P.epi[k] = epi;
     P.nf[k] = 1;
-    P.cfg[k] = pro == PRO_DIV ? g->tune_div[ax] : plain ? g->tune_psi[ax] : g->tune_r[ax];
-    P.cfg_r[k] = pro == PRO_DIV ? g->tune_div[ax] : g->tune_r[ax];
+    P.cfg[k] = pro == PRO_DIV ? g->tune_div[ax] : plain ? g->tune_psi[ax] : g->tune_p[ax];
+    P.cfg_r[k] = pro == PRO_DIV ? g->tune_div[ax] : plain ? g->tune_r[ax] : g->tune_p[ax];
   }
   P.nsw = k;
 }
@@ -617,13 +619,16 @@ int ensure_loc(ib_grid_s *g) {
 }
 
 // Autotuner: for every axis, time each candidate sweep configuration in the
-// roles the step uses it in, 1 + 3 launches each, and keep the fastest per
-// role: the plain momentum sweep on the d scratch fields (tune; tune_r, the
-// best register kernel, also serves the sweeps with an epilogue and the
-// ensembles' batched sweeps), the plain psi sweep on one scratch field with
-// the psi operator (tune_psi), and the first psi sweep with its divergence
-// prologue (tune_div), which reads the state's velocity and writes D.u and p
-// into two temporary fields.
+// five roles the step uses it in, 1 + 3 launches each, and keep the fastest
+// per role: the plain momentum sweep on the d scratch fields (tune; tune_r,
+// the best register kernel, serves the ensembles' batched plain sweeps), the
+// last momentum sweep with its u^n + e epilogue (tune_addu; u^n is the
+// scratch field itself, which every thread reads before it writes), the
+// plain psi sweep on one scratch field with the psi operator (tune_psi), the
+// first psi sweep with its divergence prologue (tune_div), which reads the
+// state's velocity and writes D.u and p into two temporary fields, and the
+// last psi sweep with its p + psi epilogue (tune_p, p in a temporary field).
+// The sweeps with a prologue or epilogue have no TMA form.
 template <typename T>
 int autotune_t(ib_grid_s *g) {
   const int d = g->dim;
@@ -645,16 +650,18 @@ int autotune_t(ib_grid_s *g) {
   sd.p = (T *)(tmp + fb);
   sd.pro_scale = T(1);
   sd.p_keep = T(1);
+  SweepArgs<T> su = sa;  // u^n + e into the scratch fields themselves
+  for (int a = 0; a < 3; ++a) su.uo[a] = (T *)g->scr[a];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = IB_OK;
   if (cudaMemsetAsync(tmp, 0, 2 * fb, g->s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(IB_ERR_CUDA, "autotune setup");
   // ms of 3 launches after one untimed launch, or < 0 on failure
-  auto time = [&](int ax, int pro, int nf, const SweepArgs<T> &a, int cfg) -> float {
-    if (launch_sweep<T>(ax, pro, EPI_STORE, nf, a, g->s, cfg) != cudaSuccess) return -1.f;
+  auto time = [&](int ax, int pro, int epi, int nf, const SweepArgs<T> &a, int cfg) -> float {
+    if (launch_sweep<T>(ax, pro, epi, nf, a, g->s, cfg) != cudaSuccess) return -1.f;
     cudaEventRecord(e0, g->s);
-    for (int r = 0; r < 3; ++r) launch_sweep<T>(ax, pro, EPI_STORE, nf, a, g->s, cfg);
+    for (int r = 0; r < 3; ++r) launch_sweep<T>(ax, pro, epi, nf, a, g->s, cfg);
     cudaEventRecord(e1, g->s);
     if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
     float ms = 0.f;
@@ -664,35 +671,38 @@ int autotune_t(ib_grid_s *g) {
   for (int ax = 0; ax < d && !rc; ++ax) {
     if (g->fixed[ax]) continue;
     sa.co = coef_of<T>(g->coef[0][ax]);
+    su.co = sa.co;
     SweepArgs<T> sp = sa;
     sp.co = coef_of<T>(g->coef[1][ax]);
     sd.co = sp.co;
-    int cand[16];
-    const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 16);
-    float best = 1e30f, best_r = 1e30f, best_p = 1e30f, best_d = 1e30f;
+    int cand[24];
+    const int nc = sweep_candidates(ax, g->n[ax], g->n[0], sizeof(T) == 8, cand, 24);
+    float best = 1e30f, best_r = 1e30f, best_p = 1e30f, best_d = 1e30f, best_u = 1e30f, best_e = 1e30f;
     for (int i = 0; i < nc && !rc; ++i) {
-      const float ms = time(ax, PRO_LOAD, d, sa, cand[i]);
-      const float mp = ms < 0.f ? ms : time(ax, PRO_LOAD, 1, sp, cand[i]);
-      const float md = mp < 0.f || cand[i] == kTmaCfg ? mp : time(ax, PRO_DIV, 1, sd, cand[i]);
-      if (ms < 0.f || mp < 0.f || md < 0.f) {
+      const bool reg = cand[i] != kTmaCfg;
+      float t[5];
+      t[0] = time(ax, PRO_LOAD, EPI_STORE, d, sa, cand[i]);
+      t[1] = t[0] < 0.f ? t[0] : time(ax, PRO_LOAD, EPI_STORE, 1, sp, cand[i]);
+      t[2] = t[1] < 0.f || !reg ? t[1] : time(ax, PRO_DIV, EPI_STORE, 1, sd, cand[i]);
+      t[3] = t[2] < 0.f || !reg ? t[2] : time(ax, PRO_LOAD, EPI_ADDU, d, su, cand[i]);
+      t[4] = t[3] < 0.f || !reg ? t[3] : time(ax, PRO_LOAD, EPI_P, 1, sd, cand[i]);
+      if (t[0] < 0.f || t[1] < 0.f || t[2] < 0.f || t[3] < 0.f || t[4] < 0.f) {
         rc = fail(IB_ERR_CUDA, "autotune launch");
         break;
       }
-      if (ms < best) {
-        best = ms;
-        g->tune[ax] = cand[i];
-      }
-      if (mp < best_p) {
-        best_p = mp;
-        g->tune_psi[ax] = cand[i];
-      }
-      if (cand[i] != kTmaCfg && ms < best_r) {
-        best_r = ms;
-        g->tune_r[ax] = cand[i];
-      }
-      if (cand[i] != kTmaCfg && md < best_d) {
-        best_d = md;
-        g->tune_div[ax] = cand[i];
+      auto keep = [&](float ms, float &b, int *slot) {
+        if (ms < b) {
+          b = ms;
+          slot[ax] = cand[i];
+        }
+      };
+      keep(t[0], best, g->tune);
+      keep(t[1], best_p, g->tune_psi);
+      if (reg) {
+        keep(t[0], best_r, g->tune_r);
+        keep(t[2], best_d, g->tune_div);
+        keep(t[3], best_u, g->tune_addu);
+        keep(t[4], best_e, g->tune_p);
       }
     }
   }
@@ -1289,13 +1299,13 @@ int ib_sweep_config(ib_grid_t g, int axis, int *cfg) {
 int ib_fix_sweep_config(ib_grid_t g, int axis, int id) {
   if (!g || axis < 0 || axis >= g->dim) return fail(IB_ERR_ARG, "bad argument");
   if (g->tuned || g->step != 0) return fail(IB_ERR_STATE, "sweep configurations are fixed before the first step");
-  int cand[16];
-  const int nc = sweep_candidates(axis, g->n[axis], g->n[0], g->prec == IB_FP64, cand, 16);
+  int cand[24];
+  const int nc = sweep_candidates(axis, g->n[axis], g->n[0], g->prec == IB_FP64, cand, 24);
   bool ok = false;
   for (int i = 0; i < nc; ++i) ok = ok || cand[i] == id;
   if (!ok) return fail(IB_ERR_ARG, "configuration %d is not a candidate for axis %d of this grid", id, axis);
   g->tune[axis] = g->tune_psi[axis] = id;
-  g->tune_r[axis] = g->tune_div[axis] = id == kTmaCfg ? -1 : id;
+  g->tune_r[axis] = g->tune_div[axis] = g->tune_addu[axis] = g->tune_p[axis] = id == kTmaCfg ? -1 : id;
   g->fixed[axis] = true;
   return IB_OK;
 }
