@@ -1,4 +1,5 @@
-"""FP32 fields on unusual 3D grids against the FP64 oracle:
+"""FP32 fields on unusual 3D grids against the FP64 oracle (and every FP64
+line-solve shape):
 
   - sizes that are not multiples of the kernels' tiles in y and z, with a
     random velocity field so every periodic neighbour carries data;
@@ -72,4 +73,46 @@ def test_rows_of_512():
     ora.step(2)
     g.step(2)
     assert_fp32(compare(ora, g), 1.0 / 512, 2)
+    g.close()
+
+
+# every strided line-solve shape (vector width, chunk, warps per line) and
+# the TMA kernel (id 11), fixed on the y axis: over three steps the rotated
+# split order puts the y sweep in every role (plain momentum, u^n + e,
+# plain psi, the divergence sweep, p + psi)
+STRIDED = {0: (1, 8, 8), 1: (2, 8, 8), 2: (4, 8, 8), 3: (1, 16, 8), 4: (2, 8, 16), 5: (4, 8, 16),
+           6: (1, 16, 16), 7: (2, 16, 16), 8: (1, 16, 32), 9: (2, 16, 32), 10: (1, 32, 16),
+           12: (1, 32, 4), 13: (2, 16, 8), 14: (1, 32, 8), 11: (1, 32, 4)}
+
+
+@pytest.mark.parametrize("ragged", [False, True])
+@pytest.mark.parametrize("cfg", sorted(STRIDED))
+def test_every_strided_shape_on_y_lines_vs_oracle(cfg, ragged):
+    vw, ch, w = STRIDED[cfg]
+    ny = ch * w - (3 if ragged else 0)       # full-length lines, or lines that leave a ragged last chunk
+    n = (32, ny, 8)
+    sc = fluid_scene(n, seed=cfg)
+    u0 = I.random_velocity(3, n, seed=100 + cfg, amplitude=0.3)
+    ora, g = make_pair(sc, "fp32", u0=u0)
+    g.fix_sweep_configs([0, cfg, 0])
+    for k in (1, 2):
+        ora.step(k)
+        g.step(k)
+        assert_fp32(compare(ora, g), 1.0 / max(n), ora.n)
+    g.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 3, 6, 8, 10])
+def test_every_fp64_strided_shape_on_y_lines_vs_oracle(cfg):
+    from test_gpu_step import assert_fp64
+    vw, ch, w = STRIDED[cfg]
+    n = (32, ch * w - 3, 8)
+    sc = fluid_scene(n, seed=cfg)
+    u0 = I.random_velocity(3, n, seed=200 + cfg, amplitude=0.3)
+    ora, g = make_pair(sc, "fp64", u0=u0)
+    g.fix_sweep_configs([0, cfg, 0])
+    for k in (1, 2):
+        ora.step(k)
+        g.step(k)
+        assert_fp64(compare(ora, g), ora.n)
     g.close()
