@@ -231,17 +231,21 @@ int ib_split_solve_noalloc(int precision, int dim, const int n[3], const double 
 
 /* The line-solve configuration a grid chose for `axis` (0..dim-1).  On its
  * first step (or first call that needs the device state) a grid times every
- * candidate configuration of its sweeps per axis on its own scratch fields and
- * keeps the fastest.  cfg[4] receives: the configuration id, then for y/z
- * lines the vector width (adjacent x lines per thread), the chunk length and
- * the warps per line, or for x lines 1, the warps per CTA (8) and the cap on
- * CTAs per SM.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
+ * candidate configuration of its sweeps per axis on its own scratch fields, in
+ * each of the step's five sweep roles (plain momentum sweep, last momentum
+ * sweep with u^n + e, plain psi sweep, first psi sweep with the divergence,
+ * last psi sweep with p + psi), and keeps the fastest per role; this call
+ * reports the plain momentum sweep's.  cfg[4] receives: the configuration
+ * id, then for y/z lines the vector width (adjacent x lines per thread), the
+ * chunk length and the warps per line, or for x lines 1, the warps per CTA (8)
+ * and the cap on CTAs per SM.  Errors: IB_ERR_ARG, IB_ERR_CUDA. */
 int ib_sweep_config(ib_grid_t g, int axis, int cfg[4]);
 
 /* Use line-solve configuration `id` (an id that ib_sweep_config reported for
- * a grid of the same size and precision) for `axis` instead of timing the
- * candidates, e.g. to reproduce a run's choice under a profiler, where timings
- * are distorted.  Only before the first step.  Errors: IB_ERR_ARG (axis, or
+ * a grid of the same size and precision) for every sweep role along `axis`
+ * instead of timing the candidates (the sweeps with a prologue or epilogue
+ * take the library's default shape where `id` is the TMA kernel, 11), e.g. to
+ * reproduce a run's choice under a profiler, where timings are distorted.  Only before the first step.  Errors: IB_ERR_ARG (axis, or
  * id not a candidate for this grid), IB_ERR_STATE (grid already stepped). */
 int ib_fix_sweep_config(ib_grid_t g, int axis, int id);
 

@@ -496,7 +496,7 @@ __global__ void k_adj_interp_bar(AdjMarkers<T> am, const T *u0, const T *u1, con
 
 static inline unsigned nb(long long work) {
   long long b = (work + 255) / 256;
-  const long long cap = 152 * 16;
+  const long long sms = device_sms(), cap = (sms > 0 ? sms : 152) * 16;
   return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 

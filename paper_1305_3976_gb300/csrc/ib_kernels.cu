@@ -367,9 +367,9 @@ __global__ void __launch_bounds__(256) k_marker_diag(int dim, const double *X0, 
 // launchers
 
 static inline unsigned grid_stride_blocks(long long work) {
-  // enough CTAs for every SM of a GB300 several times over, then grid-stride
+  // 16 CTAs per SM at most, then grid-stride
   long long b = (work + 255) / 256;
-  const long long cap = 152 * 16;
+  const long long sms = device_sms(), cap = (sms > 0 ? sms : 152) * 16;
   return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 

@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_s_b(const __grid_constant__ Ba
 
 // Sweep configurations.  Strided lines (axes 1, 2): VW adjacent x columns
 // per thread, CH elements per warp chunk, W warps per line.  x lines: the
-// grid is capped at XCAP[i] * 152 CTAs of 8 warps (warps loop over lines).
+// grid is capped at XCAP[i] CTAs of 8 warps per SM (warps loop over lines).
 struct StridedCfg {
   int vw, ch, w;
 };
@@ -913,7 +913,7 @@ cudaError_t launch_sweep_t(int axis, int nfields, const SweepArgs<T> &a, cudaStr
   if (axis == 0) {
     const long long nlines = (long long)a.n[1] * (a.dim == 3 ? a.n[2] : 1);
     const long long ctas = (nlines + 7) / 8;
-    const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
+    const long long sms = device_sms(), cap = (sms > 0 ? sms : 152) * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
     dim3 grid((unsigned)(ctas < cap ? ctas : cap), nfields);  // warps loop over lines
     const dim3 b(256);
     if (nl == 128) return launch_pdl(k_sweep_x<T, 1, PRO, EPI, true, EXT>, grid, b, 0, s, a);
@@ -966,7 +966,7 @@ cudaError_t launch_sweep_batch_t(int axis, int nfields, const SweepArgs<T> *a, i
   if (axis == 0) {
     const long long nlines = (long long)a0.n[1] * (a0.dim == 3 ? a0.n[2] : 1);
     const long long ctas = (nlines + 7) / 8;
-    const long long cap = 152LL * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
+    const long long sms = device_sms(), cap = (sms > 0 ? sms : 152) * xcap(cfg < 0 || cfg >= kXCaps ? 1 : cfg);
     for (int i = 0; i < n; ++i) g[i] = dim3((unsigned)(ctas < cap ? ctas : cap), nfields);
     const dim3 b(256);
     if (nl == 128) return launch_batch(k_sweep_x_b<T, 1, PRO, EPI, true, EXT>, a, g.data(), n, b, s);
