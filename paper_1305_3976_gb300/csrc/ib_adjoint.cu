@@ -104,18 +104,17 @@ __global__ void k_adj_div(T *q, T *divb, T *pb, T chi_mu_half, T rho_dt, T p_kee
 }
 
 // A4: u' bar (total) = ub - G(D.u' bar); also copied to Rb for the solves
+// (one thread per x index, blockIdx.y / z the other coordinates)
 template <typename T, int DIM>
-__global__ void k_adj_grad(T *ub0, T *ub1, T *ub2, T *rb0, T *rb1, T *rb2, const T *q, int nx, int ny, int nz,
-                           T ihx, T ihy, T ihz) {
-  const long long cells = (long long)nx * ny * nz;
+__global__ void __launch_bounds__(128) k_adj_grad(T *ub0, T *ub1, T *ub2, T *rb0, T *rb1, T *rb2, const T *q, int nx,
+                                                  int ny, int nz, T ihx, T ihy, T ihz) {
   T *ub[3] = {ub0, ub1, ub2}, *rb[3] = {rb0, rb1, rb2};
   const T ih[3] = {ihx, ihy, ihz};
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % nx);
-    const long long t = o / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
-    const long long dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? (long long)nx * (ny - 1) : -(long long)nx,
-                             k == 0 ? (long long)nx * ny * (nz - 1) : -(long long)nx * ny};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nx) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int o = i + nx * (j + ny * k);
+    const int dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? nx * (ny - 1) : -nx, k == 0 ? nx * ny * (nz - 1) : -nx * ny};
     const T q0 = q[o];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -130,22 +129,23 @@ __global__ void k_adj_grad(T *ub0, T *ub1, T *ub2, T *rb0, T *rb1, T *rb2, const
 //   ub += dt mu/rho L Rb;  (n > 0) pb += dt/rho D.Rb, psib = psi_w dt/rho D.Rb;
 //   V = -dt c1 Rb + Nb (the bar of N(u^n), scattered by k_adj_adv);
 //   Nb = -c2 (-dt) Rb ... = dt/2 Rb (n > 0) or 0
+// One thread per x index, blockIdx.y / z the other coordinates (32-bit
+// offsets: fields hold fewer than 2^31 elements).
 template <typename T, int DIM>
-__global__ void k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, const T *rb2, T *nb0, T *nb1, T *nb2,
-                          T *v0, T *v1, T *v2, T *pb, T *psib, int nx, int ny, int nz, T ihx, T ihy, T ihz,
-                          T dt_mu_rho, T dt_rho, T dt, T psi_w, int first) {
-  const long long cells = (long long)nx * ny * nz;
+__global__ void __launch_bounds__(128) k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, const T *rb2,
+                                                 T *nb0, T *nb1, T *nb2, T *v0, T *v1, T *v2, T *pb, T *psib, int nx,
+                                                 int ny, int nz, T ihx, T ihy, T ihz, T dt_mu_rho, T dt_rho, T dt,
+                                                 T psi_w, int first) {
   T *ub[3] = {ub0, ub1, ub2}, *nb[3] = {nb0, nb1, nb2}, *vv[3] = {v0, v1, v2};
   const T *rb[3] = {rb0, rb1, rb2};
   const T ih[3] = {ihx, ihy, ihz};
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % nx);
-    const long long t = o / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
-    const long long dp[3] = {i + 1 == nx ? 1 - nx : 1, j + 1 == ny ? (long long)nx * (1 - ny) : nx,
-                             k + 1 == nz ? (long long)nx * ny * (1 - nz) : (long long)nx * ny};
-    const long long dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? (long long)nx * (ny - 1) : -(long long)nx,
-                             k == 0 ? (long long)nx * ny * (nz - 1) : -(long long)nx * ny};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nx) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int o = i + nx * (j + ny * k);
+    const int dp[3] = {i + 1 == nx ? 1 - nx : 1, j + 1 == ny ? nx * (1 - ny) : nx,
+                       k + 1 == nz ? nx * ny * (1 - nz) : nx * ny};
+    const int dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? nx * (ny - 1) : -nx, k == 0 ? nx * ny * (nz - 1) : -nx * ny};
     T divR = T(0);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -181,75 +181,60 @@ __global__ void k_adj_rhs(T *ub0, T *ub1, T *ub2, const T *rb0, const T *rb1, co
 // The kernel gathers instead: the thread of face y of component b sums every
 // term whose target is (b, y), reading V and u around y, and adds the sum to
 // ub_b(y) once (no atomics, a fixed summation order).
+// One thread per face x index, blockIdx.y / z the other two coordinates;
+// neighbour offsets along each axis are periodic 32-bit steps (fields hold
+// fewer than 2^31 elements), combined additively across axes.
 template <typename T, int DIM>
-__global__ void k_adj_adv(T *ub0, T *ub1, T *ub2, const T *u0, const T *u1, const T *u2, const T *v0, const T *v1,
-                          const T *v2, int nx, int ny, int nz, T ihx, T ihy, T ihz) {
-  const long long cells = (long long)nx * ny * nz;
+__global__ void __launch_bounds__(128) k_adj_adv(T *ub0, T *ub1, T *ub2, const T *u0, const T *u1, const T *u2,
+                                                 const T *v0, const T *v1, const T *v2, int nx, int ny, int nz,
+                                                 T ihx, T ihy, T ihz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int o = i + nx * (j + ny * k);
   T *ub[3] = {ub0, ub1, ub2};
   const T *u[3] = {u0, u1, u2}, *vv[3] = {v0, v1, v2};
   const T ih[3] = {ihx, ihy, ihz};
-  const int n[3] = {nx, ny, nz};
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (long long)gridDim.x * blockDim.x) {
-    const int c0[3] = {(int)(o % nx), (int)((o / nx) % ny), (int)(o / ((long long)nx * ny))};
-    // linear index of y + d (periodic)
-    auto at = [&](int d0, int d1, int d2) -> long long {
-      const int d[3] = {d0, d1, d2};
-      long long idx = 0, mul = 1;
+  // offsets of y + e_a (pl) and y - e_a (mi)
+  const int pl[3] = {i + 1 == nx ? 1 - nx : 1, j + 1 == ny ? nx * (1 - ny) : nx,
+                     DIM == 3 ? (k + 1 == nz ? nx * ny * (1 - nz) : nx * ny) : 0};
+  const int mi[3] = {i == 0 ? nx - 1 : -1, j == 0 ? nx * (ny - 1) : -nx,
+                     DIM == 3 ? (k == 0 ? nx * ny * (nz - 1) : -nx * ny) : 0};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a >= DIM) break;
-        int q = c0[a] + d[a];
-        q = q < 0 ? q + n[a] : (q >= n[a] ? q - n[a] : q);
-        idx += mul * q;
-        mul *= n[a];
-      }
-      return idx;
-    };
-    // unit vector along axis a times s
-    auto e3 = [](int a, int s, int (&d)[3]) {
-      d[0] = a == 0 ? s : 0;
-      d[1] = a == 1 ? s : 0;
-      d[2] = a == 2 ? s : 0;
-    };
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) {
-      const T *vb = vv[b], *ubv = u[b];
-      T acc = T(0);
-      int db[3];
-      // a == c == b: sources y, y - b, y + b
-      {
-        e3(b, 1, db);
-        const long long yp = at(db[0], db[1], db[2]), ym = at(-db[0], -db[1], -db[2]);
-        const T uy = ubv[o], up = ubv[yp], um = ubv[ym];
-        const T sy = T(0.5) * ih[b] * vb[o], sm = T(0.5) * ih[b] * vb[ym], sp = T(0.5) * ih[b] * vb[yp];
-        acc += sy * (T(0.5) * up - T(0.5) * um);
-        acc += sm * (T(0.5) * uy + T(0.5) * (um + uy));
-        acc -= sp * (T(0.5) * uy + T(0.5) * (uy + up));
-      }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        if (a == b) continue;
-        int da[3];
-        e3(a, 1, da);
-        // c = b, axis a: S_ba A+ from source y - a, -S_ba A- from source y + a
-        const long long ya_m = at(-da[0], -da[1], -da[2]), ya_p = at(da[0], da[1], da[2]);
-        const T *ua = u[a];
-        const T Ap = T(0.5) * (ua[o] + ua[at(-db[0], -db[1], -db[2])]);
-        const T Am = T(0.5) * (ua[ya_p] + ua[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])]);
-        acc += T(0.5) * ih[a] * vb[ya_m] * Ap;
-        acc -= T(0.5) * ih[a] * vb[ya_p] * Am;
-        // c = a != b, axis b: the terms of component a's advection along b
-        // whose targets are u_b: S_ab u_a / 2 from sources y - b and
-        // y - b + a, -S_ab u_a / 2 from sources y and y + a
-        const T *va = vv[a];
-        const T shb = T(0.5) * ih[b];
-        acc += shb * va[at(-db[0], -db[1], -db[2])] * T(0.5) * ua[o];
-        acc += shb * va[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])] * T(0.5) * ua[ya_p];
-        acc -= shb * va[o] * T(0.5) * ua[at(-db[0], -db[1], -db[2])];
-        acc -= shb * va[ya_p] * T(0.5) * ua[at(da[0] - db[0], da[1] - db[1], da[2] - db[2])];
-      }
-      ub[b][o] += acc;
+  for (int b = 0; b < DIM; ++b) {
+    const T *vb = vv[b], *ubv = u[b];
+    T acc = T(0);
+    const int ymb = o + mi[b];  // y - b
+    // a == c == b: sources y, y - b, y + b
+    {
+      const int yp = o + pl[b], ym = ymb;
+      const T uy = ubv[o], up = ubv[yp], um = ubv[ym];
+      const T sy = T(0.5) * ih[b] * vb[o], sm = T(0.5) * ih[b] * vb[ym], sp = T(0.5) * ih[b] * vb[yp];
+      acc += sy * (T(0.5) * up - T(0.5) * um);
+      acc += sm * (T(0.5) * uy + T(0.5) * (um + uy));
+      acc -= sp * (T(0.5) * uy + T(0.5) * (uy + up));
     }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (a == b) continue;
+      // c = b, axis a: S_ba A+ from source y - a, -S_ba A- from source y + a
+      const int ya_m = o + mi[a], ya_p = o + pl[a], yab = o + pl[a] + mi[b];  // y - a, y + a, y + a - b
+      const T *ua = u[a];
+      const T Ap = T(0.5) * (ua[o] + ua[ymb]);
+      const T Am = T(0.5) * (ua[ya_p] + ua[yab]);
+      acc += T(0.5) * ih[a] * vb[ya_m] * Ap;
+      acc -= T(0.5) * ih[a] * vb[ya_p] * Am;
+      // c = a != b, axis b: the terms of component a's advection along b
+      // whose targets are u_b: S_ab u_a / 2 from sources y - b and
+      // y - b + a, -S_ab u_a / 2 from sources y and y + a
+      const T *va = vv[a];
+      const T shb = T(0.5) * ih[b];
+      acc += shb * va[ymb] * T(0.5) * ua[o];
+      acc += shb * va[yab] * T(0.5) * ua[ya_p];
+      acc -= shb * va[o] * T(0.5) * ua[ymb];
+      acc -= shb * va[ya_p] * T(0.5) * ua[yab];
+    }
+    ub[b][o] += acc;
   }
 }
 
@@ -510,30 +495,35 @@ template <typename T>
 cudaError_t adjoint_fields_b(const AdjFields<T> &f, cudaStream_t s) {
   k_adj_div<T><<<nb(f.cells), 256, 0, s>>>(f.q, f.divb, f.pb, f.chi_mu_half, f.rho_dt, f.p_keep, f.cells);
   if (f.dim == 2)
-    k_adj_grad<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.q, f.n[0],
-                                                 f.n[1], 1, f.ih[0], f.ih[1], T(0));
+    k_adj_grad<T, 2><<<dim3((f.n[0] + 127) / 128, f.n[1], 1), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.q, f.n[0], f.n[1], 1, f.ih[0], f.ih[1], T(0));
   else
-    k_adj_grad<T, 3><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[2], f.rb[0], f.rb[1], f.rb[2], f.q, f.n[0],
-                                                 f.n[1], f.n[2], f.ih[0], f.ih[1], f.ih[2]);
+    k_adj_grad<T, 3><<<dim3((f.n[0] + 127) / 128, f.n[1], f.n[2]), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[2], f.rb[0], f.rb[1], f.rb[2], f.q, f.n[0], f.n[1], f.n[2], f.ih[0], f.ih[1],
+        f.ih[2]);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t adjoint_fields_c(const AdjFields<T> &f, const T *const u[3], int first, cudaStream_t s) {
   if (f.dim == 2) {
-    k_adj_rhs<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.nbar[0],
+    k_adj_rhs<T, 2><<<dim3((f.n[0] + 127) / 128, f.n[1], 1), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[1], f.rb[0], f.rb[1], f.rb[1], f.nbar[0],
                                                 f.nbar[1], f.nbar[1], f.vv[0], f.vv[1], f.vv[1], f.pb, f.psib, f.n[0],
                                                 f.n[1], 1, f.ih[0], f.ih[1], T(0), f.dt_mu_rho, f.dt_rho, f.dt, f.psi_w,
                                                 first);
-    k_adj_adv<T, 2><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[1], u[0], u[1], u[1], f.vv[0], f.vv[1],
-                                                f.vv[1], f.n[0], f.n[1], 1, f.ih[0], f.ih[1], T(0));
+    k_adj_adv<T, 2><<<dim3((f.n[0] + 127) / 128, f.n[1], 1), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[1], u[0], u[1], u[1], f.vv[0], f.vv[1], f.vv[1], f.n[0], f.n[1], 1, f.ih[0], f.ih[1],
+        T(0));
   } else {
-    k_adj_rhs<T, 3><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[2], f.rb[0], f.rb[1], f.rb[2], f.nbar[0],
+    k_adj_rhs<T, 3><<<dim3((f.n[0] + 127) / 128, f.n[1], f.n[2]), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[2], f.rb[0], f.rb[1], f.rb[2], f.nbar[0],
                                                 f.nbar[1], f.nbar[2], f.vv[0], f.vv[1], f.vv[2], f.pb, f.psib, f.n[0],
                                                 f.n[1], f.n[2], f.ih[0], f.ih[1], f.ih[2], f.dt_mu_rho, f.dt_rho,
                                                 f.dt, f.psi_w, first);
-    k_adj_adv<T, 3><<<nb(f.cells), 256, 0, s>>>(f.ub[0], f.ub[1], f.ub[2], u[0], u[1], u[2], f.vv[0], f.vv[1],
-                                                f.vv[2], f.n[0], f.n[1], f.n[2], f.ih[0], f.ih[1], f.ih[2]);
+    k_adj_adv<T, 3><<<dim3((f.n[0] + 127) / 128, f.n[1], f.n[2]), 128, 0, s>>>(
+        f.ub[0], f.ub[1], f.ub[2], u[0], u[1], u[2], f.vv[0], f.vv[1], f.vv[2], f.n[0], f.n[1], f.n[2], f.ih[0],
+        f.ih[1], f.ih[2]);
   }
   return cudaGetLastError();
 }
