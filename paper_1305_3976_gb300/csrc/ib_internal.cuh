@@ -240,7 +240,8 @@ struct MarkerArgs {
   void *Uold[3];    // U^{n-1}, field precision
   void *G[3];       // nodal force at X^{n+1/2}, field precision
   // grid locations, slot 2a + o for axis a and MAC offset o (0: own axis,
-  // 1: half a cell): index of the first stencil node and the 4 node weights
+  // 1: half a cell): index of the first stencil node (in [0, n_a)) and the 4
+  // node weights
   int32_t *locI_b;  // [2d][nm] of X^n (interpolation)
   void *locI_w;     // [2d][nm][4] field precision
   int32_t *locS_b;  // [2d][nm] of X^{n+1/2} (spreading)

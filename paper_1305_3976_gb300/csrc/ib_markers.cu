@@ -21,11 +21,13 @@ namespace ibg {
 __device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
 __device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
 
-// periodic index in [0, n); one compare in the common case of an index
-// within one period of the box
-__device__ __forceinline__ int wrap_idx(int i, int n) {
+// i + d for a node index i in [0, n) and a stencil step 0 <= d <= 3 < n,
+// periodic: one compare and subtract (the stored first nodes are wrapped)
+__device__ __forceinline__ int step_wrap(int i, int n) { return i >= n ? i - n : i; }
+// i mod n in [0, n) for any i (the first stencil node of an unwrapped position)
+__device__ __forceinline__ int mod_n(int i, int n) {
   if (i >= 0 && i < n) return i;
-  int r = i % n;
+  const int r = i % n;
   return r < 0 ? r + n : r;
 }
 
@@ -67,8 +69,10 @@ __device__ __forceinline__ void weights(T f, int kernel, T (&w)[4]) {
 }
 
 // Location of coordinate X on axis a for both MAC offsets: first stencil
-// node b[2a + o] and the 4 weights w[2a + o][0..3] (stored as 4 consecutive
-// values of the field precision).
+// node b[2a + o], wrapped into [0, n_a) (positions are kept unwrapped; the
+// force kernel's nearest-image shift is exact for any whole-period offset),
+// and the 4 weights w[2a + o][0..3] (stored as 4 consecutive values of the
+// field precision).
 // With lf, the own-axis fraction f0 is stored as well.
 template <typename T>
 __device__ __forceinline__ void store_location(const MarkerArgs &m, double X, int a, long long k, int32_t *lb,
@@ -77,8 +81,8 @@ __device__ __forceinline__ void store_location(const MarkerArgs &m, double X, in
   T f0, f1, w[4];
   locate2<T>(X, m.inv_h[a], b0, f0, b1, f1);
   const long long s0 = (2 * a) * m.nm + k, s1 = (2 * a + 1) * m.nm + k;
-  lb[s0] = b0;
-  lb[s1] = b1;
+  lb[s0] = mod_n(b0, m.n[a]);
+  lb[s1] = mod_n(b1, m.n[a]);
   if (lf) lf[a * m.nm + k] = f0;
   weights<T>(f0, m.kernel, w);
   st4(lw + 4 * s0, w);
@@ -163,14 +167,14 @@ struct StencilLanes {
     if (!valid) return;
     const unsigned nm = (unsigned)m.nm;
     unsigned s = 2 * 0 + (c == 0 ? 0 : 1);
-    bx = wrap_idx(lb[s * nm + k], m.n[0]);
+    bx = lb[s * nm + k];
     ld4(lw + 4 * (s * nm + k), wx);
     s = 2 * 1 + (c == 1 ? 0 : 1);
-    yrow = wrap_idx(lb[s * nm + k] + jy, m.n[1]);
+    yrow = step_wrap(lb[s * nm + k] + jy, m.n[1]);
     wrow = lw[4 * (s * nm + k) + jy];
     if (DIM == 3) {
       s = 2 * 2 + (c == 2 ? 0 : 1);
-      zrow = wrap_idx(lb[s * nm + k] + kz, m.n[2]);
+      zrow = step_wrap(lb[s * nm + k] + kz, m.n[2]);
       wrow *= lw[4 * (s * nm + k) + kz];
     }
   }
@@ -204,11 +208,10 @@ struct StencilNodes3 {
     const unsigned nm = (unsigned)m.nm;
     const int q = lane & 3, jy = (lane >> 2) & 3, kz = lane >> 4;
     const unsigned sx = c == 0 ? 0 : 1, sy = c == 1 ? 2 : 3, sz = c == 2 ? 4 : 5;
-    int x = wrap_idx(lb[sx * nm + k], m.n[0]) + q;
-    if (x >= m.n[0]) x -= m.n[0];
-    const int y = wrap_idx(lb[sy * nm + k] + jy, m.n[1]);
+    const int x = step_wrap(lb[sx * nm + k] + q, m.n[0]);
+    const int y = step_wrap(lb[sy * nm + k] + jy, m.n[1]);
     const int bz = lb[sz * nm + k];
-    const int z0 = wrap_idx(bz + kz, m.n[2]), z1 = wrap_idx(bz + kz + 2, m.n[2]);
+    const int z0 = step_wrap(bz + kz, m.n[2]), z1 = step_wrap(bz + kz + 2, m.n[2]);
     const T wxy = lw[4 * (sx * nm + k) + q] * lw[4 * (sy * nm + k) + jy];
     w0 = wxy * lw[4 * (sz * nm + k) + kz];
     w1 = wxy * lw[4 * (sz * nm + k) + kz + 2];
