@@ -525,6 +525,10 @@ static inline unsigned nblocks(long long work, int threads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// CTA size of the update and force kernels: at 128^3 they run below one wave
+// (41 k markers), and 128-thread CTAs spread their work evenly over the SMs
+constexpr int kMarkerCta = 128;
+
 template <typename T>
 cudaError_t launch_locate(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
@@ -545,21 +549,21 @@ cudaError_t launch_interp(const MarkerArgs &m, const T *const u[3], cudaStream_t
 template <typename T>
 cudaError_t launch_update(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
-  if (m.dim == 2) return launch_pdl(k_update<T, 2>, dim3(nblocks(m.nm * 2, 256)), dim3(256), 0, s, m);
-  return launch_pdl(k_update<T, 3>, dim3(nblocks(m.nm * 3, 256)), dim3(256), 0, s, m);
+  if (m.dim == 2) return launch_pdl(k_update<T, 2>, dim3(nblocks(m.nm * 2, kMarkerCta)), dim3(kMarkerCta), 0, s, m);
+  return launch_pdl(k_update<T, 3>, dim3(nblocks(m.nm * 3, kMarkerCta)), dim3(kMarkerCta), 0, s, m);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_force(const MarkerArgs &m, cudaStream_t s) {
   if (m.nm == 0) return cudaSuccess;
-  const unsigned g = nblocks(m.nm * 8, 256);
+  const unsigned g = nblocks(m.nm * 8, kMarkerCta);
   if (m.frac_force) {
-    if (m.dim == 2) return launch_pdl(k_force<T, 2, true>, dim3(g), dim3(256), 0, s, m);
-    return launch_pdl(k_force<T, 3, true>, dim3(g), dim3(256), 0, s, m);
+    if (m.dim == 2) return launch_pdl(k_force<T, 2, true>, dim3(g), dim3(kMarkerCta), 0, s, m);
+    return launch_pdl(k_force<T, 3, true>, dim3(g), dim3(kMarkerCta), 0, s, m);
   } else {
-    if (m.dim == 2) return launch_pdl(k_force<T, 2, false>, dim3(g), dim3(256), 0, s, m);
-    return launch_pdl(k_force<T, 3, false>, dim3(g), dim3(256), 0, s, m);
+    if (m.dim == 2) return launch_pdl(k_force<T, 2, false>, dim3(g), dim3(kMarkerCta), 0, s, m);
+    return launch_pdl(k_force<T, 3, false>, dim3(g), dim3(kMarkerCta), 0, s, m);
   }
   return cudaGetLastError();
 }
@@ -598,9 +602,9 @@ cudaError_t launch_update_batch(const MarkerArgs *m, int n, cudaStream_t s) {
   if (n < 1) return cudaSuccess;
   const int d = m[0].dim;
   std::vector<dim3> g(n);
-  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * d, 256) : 0);
-  if (d == 2) return launch_batch(k_update_b<T, 2>, m, g.data(), n, dim3(256), s);
-  return launch_batch(k_update_b<T, 3>, m, g.data(), n, dim3(256), s);
+  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * d, kMarkerCta) : 0);
+  if (d == 2) return launch_batch(k_update_b<T, 2>, m, g.data(), n, dim3(kMarkerCta), s);
+  return launch_batch(k_update_b<T, 3>, m, g.data(), n, dim3(kMarkerCta), s);
 }
 
 template <typename T>
@@ -608,13 +612,13 @@ cudaError_t launch_force_batch(const MarkerArgs *m, int n, cudaStream_t s) {
   if (n < 1) return cudaSuccess;
   const int d = m[0].dim;
   std::vector<dim3> g(n);
-  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * 8, 256) : 0);
+  for (int i = 0; i < n; ++i) g[i] = dim3(m[i].nm ? nblocks(m[i].nm * 8, kMarkerCta) : 0);
   if (m[0].frac_force) {
-    if (d == 2) return launch_batch(k_force_b<T, 2, true>, m, g.data(), n, dim3(256), s);
-    return launch_batch(k_force_b<T, 3, true>, m, g.data(), n, dim3(256), s);
+    if (d == 2) return launch_batch(k_force_b<T, 2, true>, m, g.data(), n, dim3(kMarkerCta), s);
+    return launch_batch(k_force_b<T, 3, true>, m, g.data(), n, dim3(kMarkerCta), s);
   }
-  if (d == 2) return launch_batch(k_force_b<T, 2, false>, m, g.data(), n, dim3(256), s);
-  return launch_batch(k_force_b<T, 3, false>, m, g.data(), n, dim3(256), s);
+  if (d == 2) return launch_batch(k_force_b<T, 2, false>, m, g.data(), n, dim3(kMarkerCta), s);
+  return launch_batch(k_force_b<T, 3, false>, m, g.data(), n, dim3(kMarkerCta), s);
 }
 
 template <typename T>
